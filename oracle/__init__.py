@@ -1,0 +1,310 @@
+"""The oracle: plain FP64 CPU restatement of the Vecchia Gaussian-CDF method.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s cpu_baseline / reference legs may import this package.  It
+shares no code with ``paper_2007_15195_gb300`` (the CUDA library); the two
+meet only through the seeded inputs of ``paper_2007_15195_gb300.inputs``.
+
+Each wrapper below calls the C routine of the same name in ``vref.c``; the
+C header states which passage of the paper each routine follows.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import build as _build
+
+_lib = None
+
+OK, ERR_ARG, ERR_NOT_PD = 0, -1, -4
+COV_EXPONENTIAL, COV_MATERN = 0, 1
+ORDER_XY, ORDER_MAXMIN, ORDER_IDENTITY = 0, 1, 2
+
+_dp = C.POINTER(C.c_double)
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+_u32p = C.POINTER(C.c_uint32)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status, where, site=-1):
+        super().__init__("oracle %s returned %d%s" % (where, status,
+                                                      "" if site < 0 else " (site %d)" % site))
+        self.status = status
+        self.site = site
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build()
+        L = C.CDLL(path)
+        L.vref_Phi.restype = C.c_double
+        L.vref_Phi.argtypes = [C.c_double]
+        L.vref_Phi_tail.restype = C.c_double
+        L.vref_Phi_tail.argtypes = [C.c_double]
+        L.vref_Phiinv.restype = C.c_double
+        L.vref_Phiinv.argtypes = [C.c_double]
+        L.vref_Phiinv_pq.restype = C.c_double
+        L.vref_Phiinv_pq.argtypes = [C.c_double, C.c_double]
+        L.vref_Phiinv_lower.restype = C.c_double
+        L.vref_Phiinv_lower.argtypes = [C.c_double]
+        L.vref_philox4x32_10.restype = None
+        L.vref_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.vref_shifts.argtypes = [C.c_uint64, C.c_int, C.c_int, _dp]
+        L.vref_p2.restype = C.c_double
+        L.vref_p2.argtypes = [C.c_int64, C.c_int64, C.c_int]
+        L.vref_korobov_a.restype = C.c_int64
+        L.vref_korobov_a.argtypes = [C.c_int64]
+        L.vref_lattice.argtypes = [C.c_int64, C.c_int, _u32p]
+        L.vref_cov.restype = C.c_double
+        L.vref_cov.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.vref_cov_matrix.argtypes = [_dp, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, _dp]
+        L.vref_cholesky.argtypes = [C.c_int, _dp, _dp]
+        L.vref_quantize.argtypes = [_dp, C.c_int64, _i64p]
+        L.vref_order.argtypes = [_dp, C.c_int64, C.c_int, _i32p]
+        L.vref_neighbors.argtypes = [_dp, C.c_int64, C.c_int, _i32p]
+        L.vref_neighbors_of.argtypes = [_dp, C.c_int64, C.c_int64, C.c_int, _i32p]
+        L.vref_genz_sums.argtypes = [C.c_int, _dp, _dp, C.c_int64, C.c_int, _u32p, _dp, C.c_int,
+                                     _dp, _dp]
+        L.vref_genz_cdf.argtypes = [C.c_int, _dp, _dp, C.c_int64, C.c_int, C.c_uint64, _dp, _dp]
+        L.vref_vecchia_partials.argtypes = [_dp, C.c_int64, _i32p, C.c_int, C.c_int, C.c_double,
+                                            C.c_double, C.c_double, C.c_double, _dp, C.c_int64,
+                                            C.c_int, C.c_uint64, _i64p, C.c_int64, _dp, _dp, _i64p]
+        L.vref_vecchia_reduce.argtypes = [C.c_int64, C.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.vref_log_cdf.argtypes = [_dp, C.c_int64, _i32p, C.c_int, C.c_int, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, _dp, C.c_int64, C.c_int, C.c_uint64, _dp,
+                                   _dp, _dp, _i64p]
+        L.vref_full_genz.argtypes = [_dp, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, _dp, C.c_int64, C.c_int, C.c_uint64, _dp, _dp]
+        L.vref_num_threads.restype = C.c_int
+        L.vref_num_threads.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _check(st, where, site=-1):
+    if st != OK:
+        raise OracleError(st, where, site)
+
+
+# ---- univariate normal -------------------------------------------------------
+def Phi(x):
+    return lib().vref_Phi(float(x))
+
+
+def Phi_tail(x):
+    return lib().vref_Phi_tail(float(x))
+
+
+def Phiinv(p):
+    return lib().vref_Phiinv(float(p))
+
+
+def Phiinv_pq(p, q):
+    return lib().vref_Phiinv_pq(float(p), float(q))
+
+
+# ---- Philox / shifts / lattice ----------------------------------------------
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().vref_philox4x32_10(_ptr(c, _u32p), _ptr(k, _u32p), _ptr(out, _u32p))
+    return out
+
+
+def shifts(seed, S, dim):
+    out = np.zeros((S, dim), dtype=np.float64)
+    _check(lib().vref_shifts(C.c_uint64(seed), S, dim, _ptr(out, _dp)), "shifts")
+    return out
+
+
+def p2(N, a, dim=30):
+    return lib().vref_p2(N, a, dim)
+
+
+_korobov_cache = {}
+
+
+def korobov_a(N):
+    if N not in _korobov_cache:
+        _korobov_cache[N] = lib().vref_korobov_a(N)
+    return _korobov_cache[N]
+
+
+def lattice(N, dim):
+    a = korobov_a(N)
+    g = np.zeros(dim, dtype=np.uint32)
+    v = 1 % N
+    for j in range(dim):
+        g[j] = v
+        v = (v * a) % N
+    return g
+
+
+def lattice_c(N, dim):
+    """The C routine itself (recomputes the multiplier)."""
+    g = np.zeros(dim, dtype=np.uint32)
+    _check(lib().vref_lattice(N, dim, _ptr(g, _u32p)), "lattice")
+    return g
+
+
+# ---- covariance / Cholesky ---------------------------------------------------
+def cov(kind, variance, range_, nu, h):
+    return lib().vref_cov(kind, variance, range_, nu, float(h))
+
+
+def cov_matrix(sites, kind, variance, range_, nu=0.5, nugget=0.0):
+    s = _f64(sites).reshape(-1, 2)
+    n = s.shape[0]
+    out = np.zeros((n, n))
+    _check(lib().vref_cov_matrix(_ptr(s, _dp), n, kind, variance, range_, nu, nugget,
+                                 _ptr(out, _dp)), "cov_matrix")
+    return out
+
+
+def cholesky(A):
+    A = _f64(A)
+    d = A.shape[0]
+    L = np.zeros_like(A)
+    _check(lib().vref_cholesky(d, _ptr(A, _dp), _ptr(L, _dp)), "cholesky")
+    return L
+
+
+# ---- ordering / neighbours ---------------------------------------------------
+def quantize(sites):
+    s = _f64(sites).reshape(-1, 2)
+    q = np.zeros(s.shape, dtype=np.int64)
+    _check(lib().vref_quantize(_ptr(s, _dp), s.shape[0], _ptr(q, _i64p)), "quantize")
+    return q
+
+
+def order(sites, kind):
+    s = _f64(sites).reshape(-1, 2)
+    perm = np.zeros(s.shape[0], dtype=np.int32)
+    _check(lib().vref_order(_ptr(s, _dp), s.shape[0], kind, _ptr(perm, _i32p)), "order")
+    return perm
+
+
+def neighbors(sites, m):
+    s = _f64(sites).reshape(-1, 2)
+    nbr = np.full((s.shape[0], max(m, 0)), -1, dtype=np.int32)
+    _check(lib().vref_neighbors(_ptr(s, _dp), s.shape[0], m, _ptr(nbr, _i32p)), "neighbors")
+    return nbr
+
+
+def neighbors_of(sites, i, m):
+    s = _f64(sites).reshape(-1, 2)
+    out = np.full(max(m, 0), -1, dtype=np.int32)
+    _check(lib().vref_neighbors_of(_ptr(s, _dp), s.shape[0], int(i), m, _ptr(out, _i32p)),
+           "neighbors_of")
+    return out
+
+
+# ---- Genz --------------------------------------------------------------------
+def genz_sums(Sigma, u, N, S, g, delta):
+    Sig = _f64(Sigma)
+    d = Sig.shape[0]
+    u = _f64(u)
+    g = np.ascontiguousarray(g, dtype=np.uint32)
+    delta = _f64(delta)
+    dim = delta.shape[1] if delta.ndim == 2 else 1
+    num = np.zeros(S)
+    den = np.zeros(S)
+    _check(lib().vref_genz_sums(d, _ptr(Sig, _dp), _ptr(u, _dp), N, S, _ptr(g, _u32p),
+                                _ptr(delta, _dp), dim, _ptr(num, _dp), _ptr(den, _dp)), "genz_sums")
+    return num, den
+
+
+def genz_cdf(Sigma, u, N, S, seed):
+    Sig = _f64(Sigma)
+    u = _f64(u)
+    p = C.c_double()
+    rse = C.c_double()
+    _check(lib().vref_genz_cdf(Sig.shape[0], _ptr(Sig, _dp), _ptr(u, _dp), N, S, C.c_uint64(seed),
+                               C.byref(p), C.byref(rse)), "genz_cdf")
+    return p.value, rse.value
+
+
+# ---- Vecchia -----------------------------------------------------------------
+def _cov_args(cov):
+    kind, variance, range_, nu, nugget = cov
+    return int(kind), float(variance), float(range_), float(nu), float(nugget)
+
+
+def vecchia_partials(sites, nbr, m, cov, u, N, S, seed, idx=None):
+    s = _f64(sites).reshape(-1, 2)
+    D = s.shape[0]
+    nb = np.ascontiguousarray(nbr, dtype=np.int32) if m > 0 else np.zeros(1, np.int32)
+    u = _f64(u)
+    ix = None if idx is None else np.ascontiguousarray(idx, dtype=np.int64)
+    n = D if ix is None else ix.shape[0]
+    num = np.zeros((n, S))
+    den = np.zeros((n, S))
+    bad = C.c_int64(-1)
+    st = lib().vref_vecchia_partials(_ptr(s, _dp), D, _ptr(nb, _i32p), m, *_cov_args(cov),
+                                     _ptr(u, _dp), N, S, C.c_uint64(seed), _ptr(ix, _i64p),
+                                     0 if ix is None else n, _ptr(num, _dp), _ptr(den, _dp),
+                                     C.byref(bad))
+    _check(st, "vecchia_partials", bad.value)
+    return num, den
+
+
+def vecchia_reduce(num, den):
+    num = _f64(num)
+    den = _f64(den)
+    D, S = num.shape
+    lp = C.c_double()
+    se = C.c_double()
+    terms = np.zeros(D)
+    _check(lib().vref_vecchia_reduce(D, S, _ptr(num, _dp), _ptr(den, _dp), C.byref(lp),
+                                     C.byref(se), _ptr(terms, _dp)), "vecchia_reduce")
+    return lp.value, se.value, terms
+
+
+def log_cdf(sites, nbr, m, cov, u, N, S, seed, return_terms=False):
+    s = _f64(sites).reshape(-1, 2)
+    D = s.shape[0]
+    nb = np.ascontiguousarray(nbr, dtype=np.int32) if m > 0 else np.zeros(1, np.int32)
+    u = _f64(u)
+    lp = C.c_double()
+    se = C.c_double()
+    terms = np.zeros(D)
+    bad = C.c_int64(-1)
+    st = lib().vref_log_cdf(_ptr(s, _dp), D, _ptr(nb, _i32p), m, *_cov_args(cov), _ptr(u, _dp), N,
+                            S, C.c_uint64(seed), C.byref(lp), C.byref(se), _ptr(terms, _dp),
+                            C.byref(bad))
+    _check(st, "log_cdf", bad.value)
+    if return_terms:
+        return lp.value, se.value, terms
+    return lp.value, se.value
+
+
+def full_genz(sites, cov, u, N, S, seed):
+    s = _f64(sites).reshape(-1, 2)
+    u = _f64(u)
+    lp = C.c_double()
+    se = C.c_double()
+    _check(lib().vref_full_genz(_ptr(s, _dp), s.shape[0], *_cov_args(cov), _ptr(u, _dp), N, S,
+                                C.c_uint64(seed), C.byref(lp), C.byref(se)), "full_genz")
+    return lp.value, se.value
+
+
+def num_threads():
+    return lib().vref_num_threads()
+
+
+def set_threads(n):
+    """Threads for later calls (OpenMP reads the variable at first parallel region)."""
+    os.environ["OMP_NUM_THREADS"] = str(int(n))
