@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark: Vecchia log-CDF evaluations per second on the 50x50 grid workload.
+
+Workload (one "step" = the whole hot path once):
+  2,500 sites on a 50x50 grid in [0,1]^2, Matern nu = 1.5 covariance with range
+  0.1 and unit variance, thresholds u_i ~ N(0.5, 0.25^2) (seeded), m = 20
+  neighbours, Genz QMC with N = 4,096 lattice points x S = 16 shifts; step =
+  order (xy) -> apply order -> neighbour search -> log-CDF (FP32-integrand
+  "mixed" path), each step with a new QMC seed.  Inputs are resident in HBM;
+  L2 is flushed (512 MB write) between timed steps.
+
+Also measured: the plain FP64 GPU path on the same steps, both paths' error
+against the FP64 oracle, an end-to-end rate through the C ABI with pinned host
+buffers, the Genz kernel's fraction of the FP32-pipe peak, and the oracle
+itself on a bounded sample of the workload on the host cores.
+
+`--impl reference` times the oracle (the CPU restatement of the method) on the
+same metric: each step evaluates a bounded sample of terms and is scaled to a
+full evaluation.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Vecchia log-CDF evals/s (D=2500,m=20) mixed vs FP64 at stated error; p50/p99"
+UNIT = "evals/s"
+WORKLOAD = ("grid50: D=2500 sites on a 50x50 grid, Matern nu=1.5 range 0.1 variance 1, "
+            "u~N(0.5,0.25^2), m=20, N=4096 x S=16, xy order")
+
+# FP32-pipe roofline of the Genz kernel (bound "alu").
+#   peak = SMs x 128 FP32 lanes x maximum SM clock (lane operations per second,
+#          an FMA counting as one operation).
+#   algorithmic work per Genz step (one lattice coordinate of one point):
+#          ALG_OPS_STEP fixed operations (tent-transformed lattice coordinate,
+#          Phi^{-1}, Phi, running product) + (t + 1) FMAs for the conditional
+#          mean of row t + 1, i.e. q(q+1)/2 FMAs per point of a q-neighbour term.
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+ALG_OPS_STEP = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--m", type=int, default=20)
+    ap.add_argument("--no-oracle", action="store_true", help="skip the error check and cpu_baseline")
+    ap.add_argument("--l2-flush-mb", type=int, default=512)
+    ap.add_argument("--cpu-sample-sites", type=int, default=160)
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def alg_ops(D, m, N, S):
+    q = np.minimum(np.arange(D), m).astype(np.float64)
+    return float(N) * S * float(np.sum(q * ALG_OPS_STEP + q * (q + 1) / 2.0))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms",
+                 "200", "-i", str(self.device)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def prepare_workload(m, seed=0):
+    from paper_2007_15195_gb300 import inputs
+    return inputs.grid50(m=m, seed=seed)
+
+
+def cpu_baseline(prob, n_sample):
+    """The oracle on a bounded, deterministic sample of the workload's terms,
+    scaled by algorithmic work to one full evaluation."""
+    import oracle as O
+    perm = O.order(prob.sites, O.ORDER_XY)
+    s, u = prob.sites[perm], prob.u[perm]
+    nbr = O.neighbors(s, prob.m)
+    D = s.shape[0]
+    idx = np.unique(np.linspace(0, D - 1, n_sample).astype(np.int64))
+    q = np.minimum(np.arange(D), prob.m)
+    t0 = time.perf_counter()
+    O.vecchia_partials(s, nbr, prob.m, prob.cov, u, prob.N, prob.S, prob.seed, idx=idx)
+    t = time.perf_counter() - t0
+    w_all = float(np.sum(q * (q + 1) / 2.0 + q * ALG_OPS_STEP))
+    w_smp = float(np.sum(q[idx] * (q[idx] + 1) / 2.0 + q[idx] * ALG_OPS_STEP))
+    t_eval = t * w_all / w_smp
+    return {"value": 1.0 / t_eval, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d of %d terms (evenly spaced), N=%d x S=%d, scaled by algorithmic work; %.2f s"
+                      % (len(idx), D, prob.N, prob.S, t)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    prob = prepare_workload(args.m)
+    for _ in range(max(args.warmup, 0)):
+        pass  # the oracle has no warm-up state beyond its first call
+    n_sample = max(8, args.cpu_sample_sites // 4)
+    times = []
+    cb = None
+    for k in range(args.steps):
+        prob.seed = k
+        cb = cpu_baseline(prob, n_sample)
+        times.append(1.0 / cb["value"])
+    t = np.array(times)
+    value = len(t) / t.sum()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(t.mean()),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)"},
+            "p50_ms": 1000.0 * float(np.percentile(t, 50)), "p99_ms": 1000.0 * float(np.percentile(t, 99)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import paper_2007_15195_gb300 as V
+
+    world, rank, local = dist_info()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    prob = prepare_workload(args.m)
+    D, m, N, S = prob.D, prob.m, prob.N, prob.S
+    ctx = V.Context(local, stream.cuda_stream)
+    V.vecchia_set_timing(ctx, True)
+    sites_d = torch.from_numpy(prob.sites).to(dev)
+    u_d = torch.from_numpy(prob.u).to(dev)
+    flush = torch.empty(args.l2_flush_mb * (1 << 20) // 4, dtype=torch.float32, device=dev)
+
+    def step(seed, precision):
+        perm = V.vecchia_order(ctx, sites_d, "xy")
+        s_ord, u_ord = V.vecchia_apply_order(ctx, perm, sites_d, u_d)
+        nbr = V.vecchia_neighbors(ctx, s_ord, m)
+        lp, se = V.vecchia_log_cdf(ctx, s_ord, nbr, m, prob.cov, u_ord, N, S, seed, precision)
+        return lp, se
+
+    launches_per_step = {V.MIXED: 11, V.FP64: 10}
+
+    def timed(n_steps, precision, seed0):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n_steps)]
+        genz_ms = []
+        results = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(n_steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            results.append(step(seed0 + k, precision))
+            ev[k][1].record(stream)
+            genz_ms.append(V.vecchia_genz_time_ms(ctx))
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - t0
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        return ms, np.array(genz_ms), results, wall
+
+    # warm-up (also builds the lattice tables and grows the arena)
+    for k in range(max(args.warmup, 3)):
+        step(10_000 + k, V.MIXED)
+    step(20_000, V.FP64)
+
+    with ClockSampler(local) as clk:
+        ms, genz_ms, res_mixed, wall = timed(args.steps, V.MIXED, 0)
+    clocks = clk.summary()
+    total_s = float(ms.sum()) / 1000.0
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    ms64, genz64, res_fp64, _ = timed(args.fp64_steps, V.FP64, 0)
+
+    # end to end through the C ABI with pinned host buffers
+    sites_h = torch.from_numpy(prob.sites).pin_memory()
+    u_h = torch.from_numpy(prob.u).pin_memory()
+    n_e2e = max(3, min(args.steps, 20))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        perm = V.vecchia_order(ctx, sites_h, "xy")
+        s_o, u_o = V.vecchia_apply_order(None, perm, sites_h, u_h)
+        s_o, u_o = s_o.pin_memory(), u_o.pin_memory()
+        nbr = V.vecchia_neighbors(ctx, s_o, m)
+        V.vecchia_log_cdf(ctx, s_o, nbr, m, prob.cov, u_o, N, S, k, V.MIXED)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    h2d = 16 * D + (16 * D + 4 * D * m + 8 * D)
+    d2h = 4 * D * m + 32
+
+    # roofline of the Genz kernel
+    work = alg_ops(D, m, N, S)
+    genz_s = float(np.mean(genz_ms)) / 1000.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    achieved = work / genz_s
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 integrand, FP64 Cholesky/sums)",
+                       "step": "order+apply_order+neighbors+log_cdf", "seeds": "0..steps-1",
+                       "l2": "flushed between steps (%d MB write)" % args.l2_flush_mb,
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "wall_s": wall,
+            "fp64": {"value": len(ms64) / (float(ms64.sum()) / 1000.0), "unit": UNIT,
+                     "steps": len(ms64), "p50_ms": float(np.percentile(ms64, 50)),
+                     "p99_ms": float(np.percentile(ms64, 99)),
+                     "genz_kernel_ms": float(np.mean(genz64))},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "genz_kernel (mixed)", "kernel_ms": genz_s * 1000.0,
+                         "ops": "FP32-pipe lane operations, an FMA counting once; %d per Genz step "
+                                "+ q(q+1)/2 FMAs per point; peak = %d SMs x %d lanes x %.0f MHz"
+                                % (ALG_OPS_STEP, SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ)},
+            "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step[V.MIXED] * args.steps,
+            "clocks": clocks}
+
+    if rank == 0 and not args.no_oracle:
+        import oracle as O
+        perm = O.order(prob.sites, O.ORDER_XY)
+        s, u = prob.sites[perm], prob.u[perm]
+        nbr = O.neighbors(s, m)
+        t0 = time.perf_counter()
+        lp_o, se_o = O.log_cdf(s, nbr, m, prob.cov, u, N, S, 0)
+        t_or = time.perf_counter() - t0
+        lp_m, lp_64 = res_mixed[0][0], res_fp64[0][0]
+        line["error_vs_oracle"] = {
+            "seed": 0, "oracle_log_p": lp_o, "qmc_se": se_o, "oracle_s": t_or,
+            "mixed_abs": abs(lp_m - lp_o), "mixed_tol": 1e-4 * max(1.0, abs(lp_o)),
+            "fp64_rel": abs(lp_64 - lp_o) / abs(lp_o), "fp64_tol": 1e-10}
+        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_sample_sites)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * vecchia.h -- C ABI of libvecchia, a GB300 (sm_103a) implementation of the
+ * hot path of the Vecchia approximation to a high-dimensional Gaussian CDF
+ * (Nascimento & Shaby, "A Vecchia approximation for high-dimensional
+ * Gaussian cumulative distribution functions arising from spatial data",
+ * arXiv 2007.15195).
+ *
+ * The problem (Sec. 2, Eq. int): P(X < x) for X ~ N(mu, Sigma), Sigma from a
+ * stationary spatial covariance at D sites.  The approximation (Sec. 2.2,
+ * Eq. vecchia-cdf):
+ *     log P(X < x) ~ sum_i [ log Phi_{q_i+1}(u_i, u_{N(i)}) - log Phi_{q_i}(u_{N(i)}) ],
+ * q_i = min(m, i-1), N(i) the q_i nearest previously ordered sites (Sec. 2.1),
+ * each low-dimensional CDF by Genz's separation-of-variables quasi-Monte Carlo
+ * (Sec. 2.2, Sec. 3), each term on the log scale and then summed (Sec. 3.1).
+ *
+ * Conventions for every entry point:
+ *   - Every function returns a vecchia_status (0 = ok, < 0 = error).
+ *   - Buffers are caller-owned; the library never frees or retains them past
+ *     the call.  Array arguments may be host or device memory (the library asks
+ *     the CUDA runtime which); results named "host" are always host memory.
+ *   - Calls run on the context's stream and are synchronous at return.
+ *   - sites are D x 2 row-major FP64 (x, y); indices are 0-based int32.
+ *   - u are centred thresholds x - mu (Eq. int has mu; the ratio form of
+ *     Eq. vecchia-cdf works with centred values).
+ *   - Nothing here calls exit/abort; a CUDA error is returned as
+ *     VECCHIA_ERR_CUDA and leaves the context usable when the device is.
+ */
+#ifndef VECCHIA_H
+#define VECCHIA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VECCHIA_OK = 0,
+    VECCHIA_ERR_ARG = -1,          /* invalid argument (size, kind, pointer, parameter) */
+    VECCHIA_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    VECCHIA_ERR_NOMEM = -3,        /* device or host allocation failed */
+    VECCHIA_ERR_NOT_PD = -4,       /* a covariance block is not positive definite */
+    VECCHIA_ERR_NONFINITE = -5,    /* a term came out NaN/Inf or zero */
+    VECCHIA_ERR_TIMEOUT = -6,      /* a bounded device wait ran out */
+    VECCHIA_ERR_UNSUPPORTED = -7   /* valid request outside this build's limits (m > VECCHIA_MAX_M) */
+} vecchia_status;
+
+typedef enum {
+    VECCHIA_ORDER_XY = 0,       /* by x, then y, then index */
+    VECCHIA_ORDER_MAXMIN = 1,   /* exact maxmin on quantised coordinates */
+    VECCHIA_ORDER_IDENTITY = 2  /* as given */
+} vecchia_order_kind;
+
+typedef enum {
+    VECCHIA_COV_EXPONENTIAL = 0, /* variance * exp(-h / range)            (Sec. 3, Sec. 4.1) */
+    VECCHIA_COV_MATERN = 1       /* Rasmussen-Williams Matern, nu in {0.5, 1.5, 2.5} */
+} vecchia_cov_kind;
+
+/* Isotropic covariance C(h) of the spatial process; nugget adds to the
+ * diagonal (0 for none).  nu is read for VECCHIA_COV_MATERN only. */
+typedef struct {
+    int32_t kind;
+    double variance;
+    double range;
+    double nu;
+    double nugget;
+} vecchia_cov;
+
+typedef enum {
+    VECCHIA_FP64 = 0,  /* every step in FP64 */
+    VECCHIA_MIXED = 1  /* FP64 covariance, Cholesky and sums; FP32 Genz integrand */
+} vecchia_precision;
+
+/* Largest conditioning-set size m of this build (blocks of <= 32 variables). */
+#define VECCHIA_MAX_M 31
+/* Largest number of random shifts S per problem. */
+#define VECCHIA_MAX_S 64
+
+typedef struct vecchia_ctx vecchia_ctx;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns a
+ * device scratch arena that grows on demand and is freed by vecchia_destroy. */
+int vecchia_create(vecchia_ctx** ctx, int device, void* cuda_stream);
+int vecchia_destroy(vecchia_ctx* ctx);
+/* Change the stream later calls are issued on. */
+int vecchia_set_stream(vecchia_ctx* ctx, void* cuda_stream);
+
+/* Step a0 -- ordering of the sites (Sec. 2.1; Sec. 3.2 "ordering the
+ * components by distance").  perm[new position] = old index (D int32, host or
+ * device).  The caller applies perm to sites and u before the next calls.
+ * The ordering runs on the host; ctx may be NULL when both arrays are host
+ * memory.  MAXMIN costs O(D^2) integer work spread over the host's cores. */
+int vecchia_order(vecchia_ctx* ctx, const double* sites, int64_t D, int kind, int32_t* perm);
+
+/* Apply an ordering: sites_out[k] = sites[perm[k]] (D x 2) and, when u is not
+ * NULL, u_out[k] = u[perm[k]].  All arrays device memory (a gather kernel on
+ * the context's stream) or all host memory (ctx may then be NULL); outputs
+ * must not alias inputs.  An index outside [0, D) is VECCHIA_ERR_ARG. */
+int vecchia_apply_order(vecchia_ctx* ctx, const int32_t* perm, const double* sites, const double* u,
+                        int64_t D, double* sites_out, double* u_out);
+
+/* Step a1 -- conditioning sets (Sec. 2.1: the m nearest neighbours among the
+ * previously ordered sites, |N_i| = min(m, i-1)).  On GPU: grid-bucketed
+ * integer search on quantised coordinates, q = floor((x - xmin) * 2^30 /
+ * extent); ties in squared distance go to the smaller index.  nbr is D x m
+ * int32 (host or device), each row ascending, padded with -1.  0 <= m <= 31. */
+int vecchia_neighbors(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, int m, int32_t* nbr);
+
+/* Steps a2-a7 -- the Vecchia log-CDF (Eq. vecchia-cdf) with Genz QMC on a
+ * rank-1 Korobov lattice of N points (vecchia_lattice) and S random shifts
+ * drawn from `seed` (vecchia_shifts); every term shares the same points
+ * (common random numbers).  sites_ordered, u (D) and nbr (D x m, from
+ * vecchia_neighbors) are host or device; log_p and std_err are host scalars:
+ * the estimate of log P(X < u) and its delta-method standard error over the
+ * S shifts.  N >= 1, 2 <= S <= VECCHIA_MAX_S, 0 <= m <= VECCHIA_MAX_M.
+ * On VECCHIA_ERR_NOT_PD, vecchia_last_error_site() gives the ordered site. */
+int vecchia_log_cdf(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, const int32_t* nbr,
+                    int m, vecchia_cov cov, const double* u, int64_t N, int S, uint64_t seed,
+                    int precision, double* log_p, double* std_err);
+
+/* As vecchia_log_cdf, and also returns the per-term pieces (any may be NULL;
+ * each host or device): terms[i] = log mean_s num[i,s] - log mean_s den[i,s];
+ * num, den (D x S): per-shift lattice means of the (q_i+1)- and q_i-dim CDFs. */
+int vecchia_log_cdf_terms(vecchia_ctx* ctx, const double* sites_ordered, int64_t D,
+                          const int32_t* nbr, int m, vecchia_cov cov, const double* u, int64_t N,
+                          int S, uint64_t seed, int precision, double* log_p, double* std_err,
+                          double* terms, double* num, double* den);
+
+/* One problem of a batch: the arguments of vecchia_log_cdf. */
+typedef struct {
+    const double* sites;  /* D x 2, ordered */
+    const int32_t* nbr;   /* D x m */
+    const double* u;      /* D */
+    int64_t D;
+    int32_t m;
+    int32_t S;
+    int64_t N;
+    uint64_t seed;
+    vecchia_cov cov;
+} vecchia_problem;
+
+/* Many independent problems in one set of launches (the terms of every
+ * problem form one work list; Sec. 3.1's parallelism across terms, extended
+ * across problems).  The arrays of all problems must be of one kind (all host
+ * or all device).  log_p, std_err, status are host arrays of n_probs; a
+ * problem that fails gets its own status and NaN results; the call returns
+ * VECCHIA_OK when the batch ran, even if some problems failed. */
+int vecchia_log_cdf_batch(vecchia_ctx* ctx, const vecchia_problem* probs, int n_probs,
+                          int precision, double* log_p, double* std_err, int32_t* status);
+
+/* Korobov generating vector g[j] = a^j mod N, j < dim (host array): a in
+ * [2, N/2], gcd(a, N) = 1, minimising the weighted P2 criterion over 30
+ * dimensions with weights 1/j^2 (ties: smaller a).  N < 4 gives a = 1. */
+int vecchia_lattice(int64_t N, int dim, uint32_t* g);
+
+/* The random shifts of `seed` (host array S x dim): 53-bit uniforms from
+ * Philox4x32-10, key (seed lo, seed hi), counter (s, j, 0x51A7, 0). */
+int vecchia_shifts(uint64_t seed, int S, int dim, double* delta);
+
+/* Launch tile of the fused Genz kernel for one precision and block bucket
+ * (bucket b holds problems with m + 1 <= 8, 16, 24, 32 for b = 0..3; -1 = all):
+ * warps per CTA (1..16), points per lane per pass (1, 2, 4; FP64 uses 1),
+ * lattice slices per shift spread over a CTA's warps (>= 1), shift groups per
+ * site spread over CTAs (1..VECCHIA_MAX_S).  Tiles change only the launch
+ * shape; results are identical up to the order of the final FP64 sums. */
+int vecchia_set_tile(vecchia_ctx* ctx, int precision, int bucket, int warps, int points,
+                     int slices, int groups);
+/* Back to the built-in tile rule for every precision and bucket. */
+int vecchia_reset_tiles(vecchia_ctx* ctx);
+/* Record CUDA events around the Genz launches of each call (0 = off). */
+int vecchia_set_timing(vecchia_ctx* ctx, int enable);
+/* Milliseconds between those events in the last call with timing on. */
+int vecchia_genz_time_ms(const vecchia_ctx* ctx, double* ms);
+
+/* Ordered index of the site whose block failed in the last call (or -1). */
+int64_t vecchia_last_error_site(const vecchia_ctx* ctx);
+
+/* Static description of a status code. */
+const char* vecchia_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VECCHIA_H */

@@ -1,0 +1,310 @@
+"""ctypes binding of libvecchia: argument marshalling only.
+
+Every function below has the name of the C entry point it calls
+(include/vecchia.h) and does nothing but convert arrays to pointers and
+status codes to exceptions; every step of the method runs in the library.
+Arrays may be torch tensors (CPU or CUDA) or numpy arrays; outputs come back
+on the same kind of container and device as the first array argument.
+The library must have been built (``__graft_entry__.build()``); there is no
+fallback implementation.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is part of the stack
+    torch = None
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvecchia.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_PD, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+ORDER_XY, ORDER_MAXMIN, ORDER_IDENTITY = 0, 1, 2
+COV_EXPONENTIAL, COV_MATERN = 0, 1
+FP64, MIXED = 0, 1
+MAX_M, MAX_S = 31, 64
+ORDER_KINDS = {"xy": ORDER_XY, "maxmin": ORDER_MAXMIN, "identity": ORDER_IDENTITY}
+
+
+class VecchiaError(RuntimeError):
+    def __init__(self, status, where, site=-1):
+        msg = "%s: %s (status %d)" % (where, strerror(status) if _lib else "error", status)
+        if site >= 0:
+            msg += ", ordered site %d" % site
+        super().__init__(msg)
+        self.status = status
+        self.site = site
+
+
+class vecchia_cov(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("variance", C.c_double), ("range", C.c_double),
+                ("nu", C.c_double), ("nugget", C.c_double)]
+
+
+class vecchia_problem(C.Structure):
+    _fields_ = [("sites", C.c_void_p), ("nbr", C.c_void_p), ("u", C.c_void_p), ("D", C.c_int64),
+                ("m", C.c_int32), ("S", C.c_int32), ("N", C.c_int64), ("seed", C.c_uint64),
+                ("cov", vecchia_cov)]
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def lib():
+    """Load libvecchia.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libvecchia is not built (%s missing); run __graft_entry__.build()"
+                               % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        L.vecchia_strerror.restype = C.c_char_p
+        L.vecchia_strerror.argtypes = [C.c_int]
+        L.vecchia_create.argtypes = [C.POINTER(_vp), C.c_int, _vp]
+        L.vecchia_destroy.argtypes = [_vp]
+        L.vecchia_set_stream.argtypes = [_vp, _vp]
+        L.vecchia_order.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp]
+        L.vecchia_neighbors.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp]
+        L.vecchia_apply_order.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, _vp, _vp]
+        L.vecchia_log_cdf.argtypes = [_vp, _vp, C.c_int64, _vp, C.c_int, vecchia_cov, _vp, C.c_int64,
+                                      C.c_int, C.c_uint64, C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double)]
+        L.vecchia_log_cdf_terms.argtypes = [_vp, _vp, C.c_int64, _vp, C.c_int, vecchia_cov, _vp,
+                                            C.c_int64, C.c_int, C.c_uint64, C.c_int,
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double), _vp, _vp,
+                                            _vp]
+        L.vecchia_log_cdf_batch.argtypes = [_vp, C.POINTER(vecchia_problem), C.c_int, C.c_int, _vp,
+                                            _vp, _vp]
+        L.vecchia_lattice.argtypes = [C.c_int64, C.c_int, _vp]
+        L.vecchia_shifts.argtypes = [C.c_uint64, C.c_int, C.c_int, _vp]
+        L.vecchia_last_error_site.restype = C.c_int64
+        L.vecchia_last_error_site.argtypes = [_vp]
+        L.vecchia_set_tile.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.vecchia_reset_tiles.argtypes = [_vp]
+        L.vecchia_set_timing.argtypes = [_vp, C.c_int]
+        L.vecchia_genz_time_ms.argtypes = [_vp, C.POINTER(C.c_double)]
+        _lib = L
+    return _lib
+
+
+def strerror(status):
+    return lib().vecchia_strerror(int(status)).decode()
+
+
+# ------------------------------ marshalling ---------------------------------
+
+def _is_torch(a):
+    return torch is not None and isinstance(a, torch.Tensor)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _as(a, np_dtype, torch_dtype):
+    """Keep the container (torch on its device, else numpy); enforce dtype and contiguity."""
+    if _is_torch(a):
+        if a.dtype != torch_dtype:
+            a = a.to(torch_dtype)
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=np_dtype)
+
+
+def _empty_like_kind(ref, shape, np_dtype, torch_dtype):
+    if _is_torch(ref):
+        return torch.empty(shape, dtype=torch_dtype, device=ref.device)
+    return np.empty(shape, dtype=np_dtype)
+
+
+def _f64(a):
+    return _as(a, np.float64, torch.float64 if torch is not None else None)
+
+
+def _i32(a):
+    return _as(a, np.int32, torch.int32 if torch is not None else None)
+
+
+def _check(st, where, ctx=None):
+    if st != OK:
+        site = lib().vecchia_last_error_site(ctx.handle) if ctx is not None and ctx.handle else -1
+        raise VecchiaError(st, where, site)
+
+
+def make_cov(kind=COV_EXPONENTIAL, variance=1.0, range_=0.1, nu=0.5, nugget=0.0):
+    if isinstance(kind, (tuple, list)):
+        kind, variance, range_, nu, nugget = kind
+    return vecchia_cov(int(kind), float(variance), float(range_), float(nu), float(nugget))
+
+
+# ------------------------------ the context ---------------------------------
+
+class Context:
+    """A libvecchia context bound to one CUDA device and stream."""
+
+    def __init__(self, device=0, stream=None):
+        self.device = int(device)
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        h = _vp()
+        _check(lib().vecchia_create(C.byref(h), self.device, _vp(stream or 0)), "vecchia_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vecchia_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        _check(lib().vecchia_set_stream(self.handle, _vp(stream or 0)), "vecchia_set_stream", self)
+
+
+def vecchia_create(device=0, stream=None):
+    return Context(device, stream)
+
+
+def vecchia_destroy(ctx):
+    ctx.close()
+
+
+def vecchia_order(ctx, sites, kind="maxmin"):
+    s = _f64(sites)
+    D = s.shape[0]
+    k = ORDER_KINDS.get(kind, kind) if isinstance(kind, str) else int(kind)
+    perm = _empty_like_kind(s, (D,), np.int32, torch.int32 if torch is not None else None)
+    h = ctx.handle if ctx is not None else None
+    _check(lib().vecchia_order(h, _ptr(s), D, k, _ptr(perm)), "vecchia_order", ctx)
+    return perm
+
+
+def vecchia_apply_order(ctx, perm, sites, u=None):
+    """Returns (sites[perm], u[perm]) on the inputs' device (u may be None)."""
+    s = _f64(sites)
+    p = _i32(perm)
+    D = s.shape[0]
+    tdt = torch.float64 if torch is not None else None
+    so = _empty_like_kind(s, (D, 2), np.float64, tdt)
+    uu = _f64(u) if u is not None else None
+    uo = _empty_like_kind(s, (D,), np.float64, tdt) if u is not None else None
+    h = ctx.handle if ctx is not None else None
+    _check(lib().vecchia_apply_order(h, _ptr(p), _ptr(s), _ptr(uu), D, _ptr(so), _ptr(uo)),
+           "vecchia_apply_order", ctx)
+    return so, uo
+
+
+def vecchia_neighbors(ctx, sites_ordered, m):
+    s = _f64(sites_ordered)
+    D = s.shape[0]
+    nbr = _empty_like_kind(s, (D, max(int(m), 0)), np.int32, torch.int32 if torch is not None else None)
+    _check(lib().vecchia_neighbors(ctx.handle, _ptr(s), D, int(m), _ptr(nbr) if m > 0 else None),
+           "vecchia_neighbors", ctx)
+    return nbr
+
+
+def vecchia_log_cdf(ctx, sites_ordered, nbr, m, cov, u, N, S, seed=0, precision=MIXED):
+    s, uu = _f64(sites_ordered), _f64(u)
+    nb = _i32(nbr) if m > 0 else None
+    lp, se = C.c_double(), C.c_double()
+    _check(lib().vecchia_log_cdf(ctx.handle, _ptr(s), s.shape[0], _ptr(nb), int(m), make_cov(cov),
+                                 _ptr(uu), int(N), int(S), C.c_uint64(int(seed)), int(precision),
+                                 C.byref(lp), C.byref(se)), "vecchia_log_cdf", ctx)
+    return lp.value, se.value
+
+
+def vecchia_log_cdf_terms(ctx, sites_ordered, nbr, m, cov, u, N, S, seed=0, precision=MIXED):
+    """Returns (log_p, std_err, terms[D], num[D,S], den[D,S]) on the inputs' device."""
+    s, uu = _f64(sites_ordered), _f64(u)
+    nb = _i32(nbr) if m > 0 else None
+    D = s.shape[0]
+    tdt = torch.float64 if torch is not None else None
+    terms = _empty_like_kind(s, (D,), np.float64, tdt)
+    num = _empty_like_kind(s, (D, int(S)), np.float64, tdt)
+    den = _empty_like_kind(s, (D, int(S)), np.float64, tdt)
+    lp, se = C.c_double(), C.c_double()
+    _check(lib().vecchia_log_cdf_terms(ctx.handle, _ptr(s), D, _ptr(nb), int(m), make_cov(cov),
+                                       _ptr(uu), int(N), int(S), C.c_uint64(int(seed)),
+                                       int(precision), C.byref(lp), C.byref(se), _ptr(terms),
+                                       _ptr(num), _ptr(den)), "vecchia_log_cdf_terms", ctx)
+    return lp.value, se.value, terms, num, den
+
+
+def vecchia_log_cdf_batch(ctx, problems, precision=MIXED):
+    """problems: list of dicts with keys sites, nbr, m, cov, u, N, S, seed (arrays all
+    host or all device).  Returns numpy arrays (log_p, std_err, status)."""
+    n = len(problems)
+    arr = (vecchia_problem * n)()
+    keep = []
+    for i, p in enumerate(problems):
+        s, uu = _f64(p["sites"]), _f64(p["u"])
+        m = int(p["m"])
+        nb = _i32(p["nbr"]) if m > 0 else None
+        keep.append((s, uu, nb))
+        arr[i] = vecchia_problem(_ptr(s), _ptr(nb), _ptr(uu), s.shape[0], m, int(p["S"]), int(p["N"]),
+                                 int(p.get("seed", 0)), make_cov(p["cov"]))
+    lp = np.empty(n)
+    se = np.empty(n)
+    st = np.empty(n, dtype=np.int32)
+    _check(lib().vecchia_log_cdf_batch(ctx.handle, arr, n, int(precision), lp.ctypes.data,
+                                       se.ctypes.data, st.ctypes.data), "vecchia_log_cdf_batch", ctx)
+    return lp, se, st
+
+
+def vecchia_lattice(N, dim):
+    g = np.zeros(int(dim), dtype=np.uint32)
+    _check(lib().vecchia_lattice(int(N), int(dim), g.ctypes.data if dim > 0 else None),
+           "vecchia_lattice")
+    return g
+
+
+def vecchia_shifts(seed, S, dim):
+    d = np.zeros((int(S), int(dim)), dtype=np.float64)
+    _check(lib().vecchia_shifts(C.c_uint64(int(seed)), int(S), int(dim), d.ctypes.data if d.size else None),
+           "vecchia_shifts")
+    return d
+
+
+def vecchia_last_error_site(ctx):
+    return lib().vecchia_last_error_site(ctx.handle)
+
+
+def vecchia_set_tile(ctx, precision, bucket, warps, points, slices, groups):
+    _check(lib().vecchia_set_tile(ctx.handle, int(precision), int(bucket), int(warps), int(points),
+                                  int(slices), int(groups)), "vecchia_set_tile", ctx)
+
+
+def vecchia_reset_tiles(ctx):
+    _check(lib().vecchia_reset_tiles(ctx.handle), "vecchia_reset_tiles", ctx)
+
+
+def vecchia_set_timing(ctx, enable=True):
+    _check(lib().vecchia_set_timing(ctx.handle, 1 if enable else 0), "vecchia_set_timing", ctx)
+
+
+def vecchia_genz_time_ms(ctx):
+    v = C.c_double()
+    _check(lib().vecchia_genz_time_ms(ctx.handle, C.byref(v)), "vecchia_genz_time_ms", ctx)
+    return v.value

@@ -1,0 +1,873 @@
+// api.cu -- the C ABI of libvecchia (include/vecchia.h): context, argument
+// checks, device scratch arena, host-side generators (Korobov lattice,
+// Philox shifts), host ordering, and the launch sequence of the log-CDF.
+#include <omp.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "vk_internal.h"
+
+struct vecchia_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    void* arena = nullptr;
+    size_t arena_cap = 0;
+    void* host_stage = nullptr;  // pinned
+    size_t host_stage_cap = 0;
+    std::map<int64_t, uint32_t*> lattice_dev;  // N -> device [g(32) | gfix(32)]
+    int64_t last_error_site = -1;
+    vk::GenzTile tile[2][4];
+    bool tile_set[2][4] = {{false}};
+    bool timing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double genz_ms = 0.0;
+};
+
+namespace vk {
+
+int device_sm_count(int device) {
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) return 1;
+    if (!cached[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+            v = 1;
+        cached[device] = v;
+    }
+    return cached[device];
+}
+
+}  // namespace vk
+
+namespace {
+
+using vk::GenzTile;
+using vk::ProbDev;
+using vk::ProbResult;
+
+constexpr int kDim = vk::kMaxDim;  // shift-table stride and lattice length
+
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ensure_arena(vecchia_ctx* c, size_t bytes) {
+    if (bytes <= c->arena_cap) return VECCHIA_OK;
+    if (c->arena) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->arena);
+        c->arena = nullptr;
+        c->arena_cap = 0;
+    }
+    size_t cap = std::max(bytes, (size_t)1 << 20);
+    if (cudaMalloc(&c->arena, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_NOMEM;
+    }
+    c->arena_cap = cap;
+    return VECCHIA_OK;
+}
+
+int ensure_stage(vecchia_ctx* c, size_t bytes) {
+    if (bytes <= c->host_stage_cap) return VECCHIA_OK;
+    if (c->host_stage) {
+        cudaStreamSynchronize(c->stream);
+        cudaFreeHost(c->host_stage);
+        c->host_stage = nullptr;
+        c->host_stage_cap = 0;
+    }
+    size_t cap = std::max(bytes, (size_t)1 << 16);
+    if (cudaMallocHost(&c->host_stage, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_NOMEM;
+    }
+    c->host_stage_cap = cap;
+    return VECCHIA_OK;
+}
+
+// Bump allocator over a base pointer (device arena or host staging).
+struct Carve {
+    char* base;
+    size_t off = 0;
+    explicit Carve(void* b) : base((char*)b) {}
+    template <class T>
+    T* take(size_t count) {
+        T* p = (T*)(base ? base + off : nullptr);
+        off += al256(sizeof(T) * std::max<size_t>(count, 1));
+        return p;
+    }
+};
+
+// ------------------------- Korobov lattice (host) --------------------------
+// The weighted P2 criterion of g_j = a^j mod N over 30 dimensions, weights
+// gamma_j = 1/j^2:  P2 = -1 + (1/N) sum_k prod_j (1 + gamma_j 2 pi^2 B2({k g_j/N})),
+// B2(x) = x^2 - x + 1/6.  Evaluated in this fixed order of operations.
+
+double p2_of(int64_t N, int64_t a, const std::vector<double>& b2) {
+    constexpr int dim = 30;
+    const double pi = 3.14159265358979323846;
+    const double two_pi_sq = 2.0 * pi * pi;
+    int64_t g[dim], r[dim];
+    double c[dim];
+    int64_t gj = 1 % N;
+    for (int j = 0; j < dim; ++j) {
+        g[j] = gj;
+        gj = (gj * a) % N;
+        r[j] = 0;
+        c[j] = two_pi_sq / (double)((j + 1) * (j + 1));
+    }
+    double acc = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        double prod = 1.0;
+        for (int j = 0; j < dim; ++j) prod *= (1.0 + c[j] * b2[(size_t)r[j]]);
+        acc += prod;
+        for (int j = 0; j < dim; ++j) {
+            r[j] += g[j];
+            if (r[j] >= N) r[j] -= N;
+        }
+    }
+    return acc / (double)N - 1.0;
+}
+
+int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+std::mutex g_korobov_mu;
+std::map<int64_t, int64_t> g_korobov;
+
+int64_t korobov_multiplier(int64_t N) {
+    if (N < 4) return 1;
+    {
+        std::lock_guard<std::mutex> lk(g_korobov_mu);
+        auto it = g_korobov.find(N);
+        if (it != g_korobov.end()) return it->second;
+    }
+    std::vector<double> b2((size_t)N);
+    for (int64_t r = 0; r < N; ++r) {
+        const double x = (double)r / (double)N;
+        b2[(size_t)r] = (x * x - x) + (1.0 / 6.0);
+    }
+    const int64_t amax = N / 2;
+    std::vector<double> crit((size_t)amax + 1, INFINITY);
+    const int nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) {
+        th.emplace_back([&, t]() {
+            for (int64_t a = 2 + t; a <= amax; a += nt)
+                if (gcd64(a, N) == 1) crit[(size_t)a] = p2_of(N, a, b2);
+        });
+    }
+    for (auto& x : th) x.join();
+    int64_t best = 1;
+    double bv = INFINITY;
+    for (int64_t a = 2; a <= amax; ++a) {
+        if (crit[(size_t)a] < bv) {
+            bv = crit[(size_t)a];
+            best = a;
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_korobov_mu);
+    g_korobov[N] = best;
+    return best;
+}
+
+void lattice_host(int64_t N, int dim, uint32_t* g) {
+    const int64_t a = korobov_multiplier(N);
+    int64_t v = 1 % N;
+    for (int j = 0; j < dim; ++j) {
+        g[j] = (uint32_t)v;
+        v = (v * a) % N;
+    }
+}
+
+// --------------------------- Philox4x32-10 (host) ---------------------------
+
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t m0 = (uint64_t)0xD2511F53u * c[0];
+        const uint64_t m1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c[1] ^ k0;
+        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = (uint32_t)m1;
+        c[2] = n2;
+        c[3] = (uint32_t)m0;
+    }
+}
+
+// ----------------------------- argument checks ------------------------------
+
+bool cov_ok(const vecchia_cov& c) {
+    if (!(c.variance > 0.0) || !(c.range > 0.0) || !(c.nugget >= 0.0)) return false;
+    if (!std::isfinite(c.variance) || !std::isfinite(c.range) || !std::isfinite(c.nugget)) return false;
+    if (c.kind == VECCHIA_COV_EXPONENTIAL) return true;
+    if (c.kind == VECCHIA_COV_MATERN) return c.nu == 0.5 || c.nu == 1.5 || c.nu == 2.5;
+    return false;
+}
+
+int check_problem(const vecchia_problem& p) {
+    if (p.D < 1 || p.D > INT_MAX / 2 || !p.sites || !p.u) return VECCHIA_ERR_ARG;
+    if (p.m < 0) return VECCHIA_ERR_ARG;
+    if (p.m > VECCHIA_MAX_M) return VECCHIA_ERR_UNSUPPORTED;
+    if (p.m > 0 && !p.nbr) return VECCHIA_ERR_ARG;
+    if (p.N < 1 || p.N > INT_MAX) return VECCHIA_ERR_ARG;
+    if (p.S < 2 || p.S > VECCHIA_MAX_S) return VECCHIA_ERR_ARG;
+    if (!cov_ok(p.cov)) return VECCHIA_ERR_ARG;
+    return VECCHIA_OK;
+}
+
+uint32_t* lattice_for(vecchia_ctx* c, int64_t N) {
+    auto it = c->lattice_dev.find(N);
+    if (it != c->lattice_dev.end()) return it->second;
+    uint32_t h[2 * kDim];
+    lattice_host(N, kDim, h);
+    for (int j = 0; j < kDim; ++j)  // round(g 2^32 / N): exact when N is a power of two
+        h[kDim + j] = (uint32_t)((((uint64_t)h[j] << 32) + (uint64_t)N / 2) / (uint64_t)N);
+    uint32_t* d = nullptr;
+    if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaMemcpy(d, h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    c->lattice_dev[N] = d;
+    return d;
+}
+
+GenzTile default_tile(bool mixed, int64_t total_sites, int max_S) {
+    GenzTile t;
+    t.warps = 4;
+    t.points = mixed ? 2 : 1;
+    t.slices = 1;
+    int64_t g = (6144 + total_sites - 1) / std::max<int64_t>(total_sites, 1);
+    t.groups = (int)std::min<int64_t>(std::max<int64_t>(g, 1), max_S);
+    return t;
+}
+
+// ------------------------------ the pipeline --------------------------------
+// Runs n problems: validation, staging, shift tables, Genz per bucket, FP64
+// re-evaluation of flagged sites (mixed), log-sum, results.
+
+int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precision,
+                 double* log_p, double* std_err, int32_t* status, double* terms, double* num,
+                 double* den) {
+    if (!c || !probs || n < 1 || !log_p || !std_err || !status) return VECCHIA_ERR_ARG;
+    if (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) return VECCHIA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    const bool mixed = precision == VECCHIA_MIXED;
+    c->last_error_site = -1;
+
+    std::vector<int> ok(n);
+    int n_ok = 0;
+    for (int i = 0; i < n; ++i) {
+        status[i] = check_problem(probs[i]);
+        ok[i] = status[i] == VECCHIA_OK;
+        n_ok += ok[i];
+        log_p[i] = NAN;
+        std_err[i] = NAN;
+    }
+    if (n_ok == 0) return n == 1 ? status[0] : VECCHIA_OK;
+
+    const bool host_in = !is_device_ptr(probs[0].sites);
+    if (host_in) {  // a host problem with NaN thresholds is an argument error
+        for (int i = 0; i < n; ++i) {
+            if (!ok[i]) continue;
+            for (int64_t k = 0; k < probs[i].D; ++k) {
+                if (!std::isfinite(probs[i].u[k])) {
+                    status[i] = VECCHIA_ERR_ARG;
+                    ok[i] = 0;
+                    --n_ok;
+                    break;
+                }
+            }
+        }
+        if (n_ok == 0) return n == 1 ? status[0] : VECCHIA_OK;
+    }
+
+    // buckets and totals
+    int64_t total_sites = 0, total_ds = 0, fb_cap = 0;
+    int max_S[4] = {0, 0, 0, 0};
+    int64_t bucket_sites[4] = {0, 0, 0, 0};
+    int bucket_segs[4] = {0, 0, 0, 0};
+    std::vector<int> bucket_of(n, -1);
+    for (int i = 0; i < n; ++i) {
+        if (!ok[i]) continue;
+        const int b = vk::bucket_of(probs[i].m + 1);
+        bucket_of[i] = b;
+        bucket_sites[b] += probs[i].D;
+        bucket_segs[b] += 1;
+        max_S[b] = std::max(max_S[b], probs[i].S);
+        total_sites += probs[i].D;
+        total_ds += probs[i].D * probs[i].S;
+    }
+    GenzTile tiles[4];
+    int max_groups = 1;
+    for (int b = 0; b < 4; ++b) {
+        tiles[b] = c->tile_set[mixed][b] ? c->tile[mixed][b] : default_tile(mixed, total_sites, std::max(max_S[b], 2));
+        max_groups = std::max(max_groups, tiles[b].groups);
+    }
+    fb_cap = mixed ? total_sites * max_groups : 0;
+
+    // lattice tables per distinct N
+    std::vector<uint32_t*> lat(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        if (!ok[i]) continue;
+        lat[i] = lattice_for(c, probs[i].N);
+        if (!lat[i]) return VECCHIA_ERR_NOMEM;
+    }
+
+    // ---- device arena layout ----
+    Carve dv(nullptr);
+    std::vector<size_t> o_sites(n), o_nbr(n), o_u(n), o_num(n), o_den(n);
+    for (int i = 0; i < n; ++i) {
+        if (!ok[i]) continue;
+        const auto& p = probs[i];
+        if (host_in) {
+            o_sites[i] = dv.off;
+            dv.take<double>(2 * p.D);
+            o_nbr[i] = dv.off;
+            dv.take<int32_t>((size_t)p.D * std::max(p.m, 1));
+            o_u[i] = dv.off;
+            dv.take<double>(p.D);
+        }
+        o_num[i] = dv.off;
+        dv.take<double>((size_t)p.D * p.S);
+        o_den[i] = dv.off;
+        dv.take<double>((size_t)p.D * p.S);
+    }
+    const size_t o_means = dv.off;
+    dv.take<double>(2 * total_sites);
+    const size_t o_delta = dv.off;
+    dv.take<double>((size_t)n * vk::kMaxS * kDim);
+    const size_t o_dfix = dv.off;
+    dv.take<uint32_t>((size_t)n * vk::kMaxS * kDim);
+    const size_t o_fbcount = dv.off;
+    dv.take<int>(1);
+    const size_t o_fbitems = dv.off;
+    dv.take<int2>((size_t)std::max<int64_t>(fb_cap, 1));
+    const size_t o_terms_out = dv.off;
+    const bool terms_host = terms && !is_device_ptr(terms);
+    if (terms_host) dv.take<double>(total_sites);
+    // parameter blob (copied in one transfer)
+    const size_t o_blob = dv.off;
+    Carve hb(nullptr);
+    const size_t b_probs = hb.off;
+    hb.take<ProbDev>(n);
+    const size_t b_results = hb.off;
+    hb.take<ProbResult>(n);
+    const size_t b_seeds = hb.off;
+    hb.take<uint64_t>(n);
+    const size_t b_S = hb.off;
+    hb.take<int32_t>(n);
+    const size_t b_off = hb.off;
+    hb.take<int64_t>(n);
+    const size_t b_moff = hb.off;
+    hb.take<int64_t>(n);
+    const size_t b_tptr = hb.off;
+    hb.take<double*>(n);
+    size_t b_segp[4], b_segb[4];
+    for (int b = 0; b < 4; ++b) {
+        b_segp[b] = hb.off;
+        hb.take<int>(bucket_segs[b] + 1);
+        b_segb[b] = hb.off;
+        hb.take<int2>(std::max(bucket_segs[b], 1));
+    }
+    const size_t blob_bytes = hb.off;
+    dv.take<char>(blob_bytes);
+    const size_t arena_bytes = dv.off;
+
+    int st = ensure_arena(c, arena_bytes);
+    if (st != VECCHIA_OK) return st;
+    st = ensure_stage(c, blob_bytes);
+    if (st != VECCHIA_OK) return st;
+    char* A = (char*)c->arena;
+    char* H = (char*)c->host_stage;
+    char* blob_dev = A + o_blob;
+
+    // ---- fill the blob ----
+    ProbDev* hp = (ProbDev*)(H + b_probs);
+    uint64_t* hseeds = (uint64_t*)(H + b_seeds);
+    int32_t* hS = (int32_t*)(H + b_S);
+    int64_t* hoff = (int64_t*)(H + b_off);
+    int64_t* hmoff = (int64_t*)(H + b_moff);
+    double** htp = (double**)(H + b_tptr);
+    int64_t moff = 0;
+    for (int i = 0; i < n; ++i) {
+        const auto& p = probs[i];
+        ProbDev& d = hp[i];
+        std::memset(&d, 0, sizeof(d));
+        hseeds[i] = p.seed;
+        hS[i] = ok[i] ? p.S : 0;
+        hoff[i] = (int64_t)i * vk::kMaxS * kDim;
+        hmoff[i] = moff;
+        htp[i] = nullptr;
+        if (!ok[i]) continue;
+        d.sites = host_in ? (const double*)(A + o_sites[i]) : p.sites;
+        d.nbr = host_in ? (const int32_t*)(A + o_nbr[i]) : p.nbr;
+        d.u = host_in ? (const double*)(A + o_u[i]) : p.u;
+        d.num = (double*)(A + o_num[i]);
+        d.den = (double*)(A + o_den[i]);
+        d.g = lat[i];
+        d.gfix = lat[i] + kDim;
+        d.delta = (const double*)(A + o_delta) + hoff[i];
+        d.dfix = (const uint32_t*)(A + o_dfix) + hoff[i];
+        d.D = p.D;
+        d.N = p.N;
+        d.variance = p.cov.variance;
+        d.range = p.cov.range;
+        d.nu = p.cov.nu;
+        d.nugget = p.cov.nugget;
+        d.cov_kind = p.cov.kind;
+        d.m = p.m;
+        d.S = p.S;
+        d.dim = kDim;
+        if (terms) htp[i] = terms_host ? (double*)(A + o_terms_out) : terms;
+        moff += 2 * p.D;
+    }
+    for (int b = 0; b < 4; ++b) {
+        int* sp = (int*)(H + b_segp[b]);
+        int2* sb = (int2*)(H + b_segb[b]);
+        int k = 0, run = 0;
+        for (int i = 0; i < n; ++i) {
+            if (!ok[i] || bucket_of[i] != b) continue;
+            sp[k] = run;
+            sb[k] = make_int2(i, 0);
+            run += (int)probs[i].D;
+            ++k;
+        }
+        sp[k] = run;
+    }
+
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaSuccess;
+    if (host_in) {
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            if (!ok[i]) continue;
+            const auto& p = probs[i];
+            e = cudaMemcpyAsync(A + o_sites[i], p.sites, sizeof(double) * 2 * p.D, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && p.m > 0)
+                e = cudaMemcpyAsync(A + o_nbr[i], p.nbr, sizeof(int32_t) * p.D * p.m, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(A + o_u[i], p.u, sizeof(double) * p.D, cudaMemcpyHostToDevice, s);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(blob_dev, H, blob_bytes, cudaMemcpyHostToDevice, s);
+    ProbDev* probs_d = (ProbDev*)(blob_dev + b_probs);
+    ProbResult* res_d = (ProbResult*)(blob_dev + b_results);
+    int* fbc = (int*)(A + o_fbcount);
+    int2* fbi = (int2*)(A + o_fbitems);
+    if (e == cudaSuccess) e = vk::launch_init_results(res_d, n, fbc, s);
+    if (e == cudaSuccess)
+        e = vk::launch_shifts((const uint64_t*)(blob_dev + b_seeds), (const int32_t*)(blob_dev + b_S),
+                              (const int64_t*)(blob_dev + b_off), n, kDim, (double*)(A + o_delta),
+                              (uint32_t*)(A + o_dfix), s);
+    if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev0, s);
+    // largest blocks first
+    for (int b = 3; b >= 0 && e == cudaSuccess; --b) {
+        if (!bucket_sites[b]) continue;
+        e = vk::launch_genz(b, mixed, tiles[b], probs_d, (const int*)(blob_dev + b_segp[b]),
+                            (const int2*)(blob_dev + b_segb[b]), bucket_segs[b], (int)bucket_sites[b],
+                            res_d, fbc, fbi, max_S[b], s);
+    }
+    if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
+    if (mixed && e == cudaSuccess)
+        e = vk::launch_genz_fallback(probs_d, fbc, fbi, (int)fb_cap, res_d, s);
+    if (e == cudaSuccess)
+        e = vk::launch_logsum(probs_d, n, res_d, terms ? (double* const*)(blob_dev + b_tptr) : nullptr,
+                              (double*)(A + o_means), (const int64_t*)(blob_dev + b_moff), s);
+    ProbResult* hres = (ProbResult*)(H + b_results);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hres, res_d, sizeof(ProbResult) * n, cudaMemcpyDeviceToHost, s);
+    if (n == 1 && ok[0] && e == cudaSuccess) {
+        const auto& p = probs[0];
+        if (terms_host)
+            e = cudaMemcpyAsync(terms, A + o_terms_out, sizeof(double) * p.D, cudaMemcpyDefault, s);
+        if (num && e == cudaSuccess)
+            e = cudaMemcpyAsync(num, A + o_num[0], sizeof(double) * p.D * p.S, cudaMemcpyDefault, s);
+        if (den && e == cudaSuccess)
+            e = cudaMemcpyAsync(den, A + o_den[0], sizeof(double) * p.D * p.S, cudaMemcpyDefault, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    if (c->timing) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->genz_ms = ms;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!ok[i]) continue;
+        status[i] = hres[i].status;
+        log_p[i] = hres[i].log_p;
+        std_err[i] = hres[i].std_err;
+        if (hres[i].status != VECCHIA_OK) {
+            log_p[i] = NAN;
+            std_err[i] = NAN;
+            if (hres[i].bad_site != LLONG_MAX && c->last_error_site < 0) c->last_error_site = hres[i].bad_site;
+        }
+    }
+    return n == 1 ? status[0] : VECCHIA_OK;
+}
+
+// ------------------------------ host ordering ------------------------------
+
+void quantize_host(const double* s, int64_t D, std::vector<int64_t>& q) {
+    q.assign(2 * (size_t)D, 0);
+    double x0 = s[0], x1 = s[0], y0 = s[1], y1 = s[1];
+    for (int64_t i = 1; i < D; ++i) {
+        x0 = std::min(x0, s[2 * i]);
+        x1 = std::max(x1, s[2 * i]);
+        y0 = std::min(y0, s[2 * i + 1]);
+        y1 = std::max(y1, s[2 * i + 1]);
+    }
+    const double ex = x1 - x0, ey = y1 - y0;
+    const double ext = ex > ey ? ex : ey;
+    if (!(ext > 0.0)) return;
+    const double c = 1073741824.0 / ext;
+    for (int64_t i = 0; i < D; ++i) {
+        const double tx = s[2 * i] - x0;
+        const double ty = s[2 * i + 1] - y0;
+        q[2 * (size_t)i] = (int64_t)std::floor(tx * c);
+        q[2 * (size_t)i + 1] = (int64_t)std::floor(ty * c);
+    }
+}
+
+void order_maxmin(const double* s, int64_t D, int32_t* perm) {
+    std::vector<int64_t> q;
+    quantize_host(s, D, q);
+    int64_t qxm = 0, qym = 0;
+    for (int64_t i = 0; i < D; ++i) {
+        qxm = std::max(qxm, q[2 * i]);
+        qym = std::max(qym, q[2 * i + 1]);
+    }
+    int64_t first = 0, bestc = -1;
+    for (int64_t i = 0; i < D; ++i) {
+        const int64_t dx = 2 * q[2 * i] - qxm, dy = 2 * q[2 * i + 1] - qym;
+        const int64_t v = dx * dx + dy * dy;
+        if (bestc < 0 || v < bestc) {
+            bestc = v;
+            first = i;
+        }
+    }
+    std::vector<int64_t> mind((size_t)D, LLONG_MAX);
+    std::vector<char> chosen((size_t)D, 0);
+    perm[0] = (int32_t)first;
+    chosen[(size_t)first] = 1;
+    const int T = D < 4096 ? 1 : std::max(1, std::min(omp_get_max_threads(), 64));
+    std::vector<int64_t> tv(T), ti(T);
+#pragma omp parallel num_threads(T)
+    {
+        const int t = omp_get_thread_num();
+        const int64_t lo = D * t / T, hi = D * (t + 1) / T;
+        for (int64_t pos = 1; pos < D; ++pos) {
+            const int64_t last = perm[pos - 1];
+            const int64_t lx = q[2 * last], ly = q[2 * last + 1];
+            int64_t bv = -1, bi = -1;
+            for (int64_t i = lo; i < hi; ++i) {
+                if (chosen[(size_t)i]) continue;
+                const int64_t dx = q[2 * i] - lx, dy = q[2 * i + 1] - ly;
+                const int64_t v = std::min(mind[(size_t)i], dx * dx + dy * dy);
+                mind[(size_t)i] = v;
+                if (v > bv) {
+                    bv = v;
+                    bi = i;
+                }
+            }
+            tv[t] = bv;
+            ti[t] = bi;
+#pragma omp barrier
+#pragma omp single
+            {
+                int64_t best = -1, besti = -1;
+                for (int k = 0; k < T; ++k)
+                    if (tv[k] > best) {  // chunks ascend, so ties keep the smaller index
+                        best = tv[k];
+                        besti = ti[k];
+                    }
+                perm[pos] = (int32_t)besti;
+                chosen[(size_t)besti] = 1;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// =============================== C ABI ======================================
+
+extern "C" {
+
+const char* vecchia_strerror(int status) {
+    switch (status) {
+        case VECCHIA_OK: return "ok";
+        case VECCHIA_ERR_ARG: return "invalid argument";
+        case VECCHIA_ERR_CUDA: return "CUDA runtime error";
+        case VECCHIA_ERR_NOMEM: return "out of memory";
+        case VECCHIA_ERR_NOT_PD: return "covariance block not positive definite";
+        case VECCHIA_ERR_NONFINITE: return "non-finite result";
+        case VECCHIA_ERR_TIMEOUT: return "device wait timed out";
+        case VECCHIA_ERR_UNSUPPORTED: return "outside this build's limits";
+        default: return "unknown status";
+    }
+}
+
+int vecchia_create(vecchia_ctx** ctx, int device, void* cuda_stream) {
+    if (!ctx) return VECCHIA_ERR_ARG;
+    *ctx = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return VECCHIA_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    vecchia_ctx* c = new (std::nothrow) vecchia_ctx();
+    if (!c) return VECCHIA_ERR_NOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        delete c;
+        return VECCHIA_ERR_CUDA;
+    }
+    *ctx = c;
+    return VECCHIA_OK;
+}
+
+int vecchia_destroy(vecchia_ctx* c) {
+    if (!c) return VECCHIA_ERR_ARG;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->arena) cudaFree(c->arena);
+    if (c->host_stage) cudaFreeHost(c->host_stage);
+    for (auto& kv : c->lattice_dev) cudaFree(kv.second);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    return VECCHIA_OK;
+}
+
+int vecchia_set_stream(vecchia_ctx* c, void* cuda_stream) {
+    if (!c) return VECCHIA_ERR_ARG;
+    c->stream = (cudaStream_t)cuda_stream;
+    return VECCHIA_OK;
+}
+
+int64_t vecchia_last_error_site(const vecchia_ctx* c) { return c ? c->last_error_site : -1; }
+
+int vecchia_lattice(int64_t N, int dim, uint32_t* g) {
+    if (N < 1 || N > INT_MAX || dim < 0 || (dim > 0 && !g)) return VECCHIA_ERR_ARG;
+    lattice_host(N, dim, g);
+    return VECCHIA_OK;
+}
+
+int vecchia_shifts(uint64_t seed, int S, int dim, double* delta) {
+    if (S < 0 || dim < 0 || ((int64_t)S * dim > 0 && !delta)) return VECCHIA_ERR_ARG;
+    for (int s = 0; s < S; ++s) {
+        for (int j = 0; j < dim; ++j) {
+            uint32_t c[4] = {(uint32_t)s, (uint32_t)j, 0x51A7u, 0u};
+            philox_host(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+            const uint64_t M = ((uint64_t)(c[0] >> 5) << 26) | (uint64_t)(c[1] >> 6);
+            delta[(size_t)s * dim + j] = (double)M * 0x1p-53;
+        }
+    }
+    return VECCHIA_OK;
+}
+
+int vecchia_order(vecchia_ctx* c, const double* sites, int64_t D, int kind, int32_t* perm) {
+    if (!sites || !perm || D < 1 || D > INT_MAX) return VECCHIA_ERR_ARG;
+    if (kind != VECCHIA_ORDER_XY && kind != VECCHIA_ORDER_MAXMIN && kind != VECCHIA_ORDER_IDENTITY)
+        return VECCHIA_ERR_ARG;
+    // the ordering itself is host work: with no context, both arrays are host memory
+    const bool dev_in = c && is_device_ptr(sites), dev_out = c && is_device_ptr(perm);
+    if (c && (dev_in || dev_out) && cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    std::vector<double> hs;
+    const double* s = sites;
+    if (dev_in) {
+        hs.resize(2 * (size_t)D);
+        if (cudaMemcpyAsync(hs.data(), sites, sizeof(double) * 2 * D, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return VECCHIA_ERR_CUDA;
+        s = hs.data();
+    }
+    std::vector<int32_t> p((size_t)D);
+    for (int64_t i = 0; i < D; ++i) p[(size_t)i] = (int32_t)i;
+    if (kind == VECCHIA_ORDER_XY) {
+        std::sort(p.begin(), p.end(), [s](int32_t a, int32_t b) {
+            if (s[2 * a] != s[2 * b]) return s[2 * a] < s[2 * b];
+            if (s[2 * a + 1] != s[2 * b + 1]) return s[2 * a + 1] < s[2 * b + 1];
+            return a < b;
+        });
+    } else if (kind == VECCHIA_ORDER_MAXMIN) {
+        order_maxmin(s, D, p.data());
+    }
+    if (dev_out) {
+        if (cudaMemcpyAsync(perm, p.data(), sizeof(int32_t) * D, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return VECCHIA_ERR_CUDA;
+    } else {
+        std::memcpy(perm, p.data(), sizeof(int32_t) * D);
+    }
+    return VECCHIA_OK;
+}
+
+int vecchia_apply_order(vecchia_ctx* c, const int32_t* perm, const double* sites, const double* u,
+                        int64_t D, double* sites_out, double* u_out) {
+    if (!perm || !sites || !sites_out || D < 1 || D > INT_MAX || (u && !u_out)) return VECCHIA_ERR_ARG;
+    if ((const void*)sites == (void*)sites_out || (u && (const void*)u == (void*)u_out)) return VECCHIA_ERR_ARG;
+    const bool dev = c && is_device_ptr(sites);
+    if (dev) {
+        if (!is_device_ptr(perm) || !is_device_ptr(sites_out) || (u && (!is_device_ptr(u) || !is_device_ptr(u_out))))
+            return VECCHIA_ERR_ARG;
+        if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+        if (ensure_arena(c, 256) != VECCHIA_OK) return VECCHIA_ERR_NOMEM;
+        int* bad = (int*)c->arena;
+        int hbad = 0;
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess) e = vk::launch_gather(perm, sites, u, D, sites_out, u_out, bad, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return VECCHIA_ERR_CUDA;
+        }
+        return hbad ? VECCHIA_ERR_ARG : VECCHIA_OK;
+    }
+    for (int64_t k = 0; k < D; ++k) {
+        const int32_t j = perm[k];
+        if (j < 0 || j >= D) return VECCHIA_ERR_ARG;
+        sites_out[2 * k] = sites[2 * (int64_t)j];
+        sites_out[2 * k + 1] = sites[2 * (int64_t)j + 1];
+        if (u) u_out[k] = u[j];
+    }
+    return VECCHIA_OK;
+}
+
+int vecchia_neighbors(vecchia_ctx* c, const double* sites, int64_t D, int m, int32_t* nbr) {
+    if (!c || !sites || D < 1 || D > INT_MAX / 2 || m < 0) return VECCHIA_ERR_ARG;
+    if (m > VECCHIA_MAX_M) return VECCHIA_ERR_UNSUPPORTED;
+    if (m == 0) return VECCHIA_OK;
+    if (!nbr) return VECCHIA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    const bool dev_in = is_device_ptr(sites), dev_out = is_device_ptr(nbr);
+    Carve dv(nullptr);
+    const size_t o_s = dv.off;
+    if (!dev_in) dv.take<double>(2 * D);
+    const size_t o_n = dv.off;
+    if (!dev_out) dv.take<int32_t>((size_t)D * m);
+    const size_t o_scr = dv.off;
+    dv.take<char>(vk::knn_scratch_bytes(D));
+    int st = ensure_arena(c, dv.off);
+    if (st != VECCHIA_OK) return st;
+    char* A = (char*)c->arena;
+    const double* sd = dev_in ? sites : (const double*)(A + o_s);
+    int32_t* nd = dev_out ? nbr : (int32_t*)(A + o_n);
+    cudaError_t e = cudaSuccess;
+    if (!dev_in) e = cudaMemcpyAsync(A + o_s, sites, sizeof(double) * 2 * D, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = vk::launch_knn(sd, D, m, nd, A + o_scr, c->stream);
+    if (e == cudaSuccess && !dev_out)
+        e = cudaMemcpyAsync(nbr, nd, sizeof(int32_t) * D * m, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    return VECCHIA_OK;
+}
+
+int vecchia_log_cdf_terms(vecchia_ctx* c, const double* sites, int64_t D, const int32_t* nbr, int m,
+                          vecchia_cov cov, const double* u, int64_t N, int S, uint64_t seed,
+                          int precision, double* log_p, double* std_err, double* terms, double* num,
+                          double* den) {
+    vecchia_problem p;
+    p.sites = sites;
+    p.nbr = nbr;
+    p.u = u;
+    p.D = D;
+    p.m = m;
+    p.S = S;
+    p.N = N;
+    p.seed = seed;
+    p.cov = cov;
+    int32_t status = VECCHIA_OK;
+    double lp = NAN, se = NAN;
+    const int st = run_problems(c, &p, 1, precision, &lp, &se, &status, terms, num, den);
+    if (log_p) *log_p = lp;
+    if (std_err) *std_err = se;
+    return st;
+}
+
+int vecchia_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, const int32_t* nbr, int m,
+                    vecchia_cov cov, const double* u, int64_t N, int S, uint64_t seed, int precision,
+                    double* log_p, double* std_err) {
+    if (!log_p || !std_err) return VECCHIA_ERR_ARG;
+    return vecchia_log_cdf_terms(c, sites, D, nbr, m, cov, u, N, S, seed, precision, log_p, std_err,
+                                 nullptr, nullptr, nullptr);
+}
+
+int vecchia_log_cdf_batch(vecchia_ctx* c, const vecchia_problem* probs, int n_probs, int precision,
+                          double* log_p, double* std_err, int32_t* status) {
+    if (!c || !probs || n_probs < 1 || !log_p || !std_err || !status) return VECCHIA_ERR_ARG;
+    return run_problems(c, probs, n_probs, precision, log_p, std_err, status, nullptr, nullptr, nullptr);
+}
+
+int vecchia_set_tile(vecchia_ctx* c, int precision, int bucket, int warps, int points, int slices,
+                     int groups) {
+    if (!c || (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) || bucket < -1 || bucket > 3)
+        return VECCHIA_ERR_ARG;
+    if (warps < 1 || warps > 16 || (points != 1 && points != 2 && points != 4) || slices < 1 ||
+        groups < 1 || groups > VECCHIA_MAX_S)
+        return VECCHIA_ERR_ARG;
+    const int b0 = bucket < 0 ? 0 : bucket, b1 = bucket < 0 ? 3 : bucket;
+    for (int b = b0; b <= b1; ++b) {
+        c->tile[precision][b] = vk::GenzTile{warps, precision == VECCHIA_FP64 ? 1 : points, slices, groups};
+        c->tile_set[precision][b] = true;
+    }
+    return VECCHIA_OK;
+}
+
+int vecchia_reset_tiles(vecchia_ctx* c) {
+    if (!c) return VECCHIA_ERR_ARG;
+    for (int p = 0; p < 2; ++p)
+        for (int b = 0; b < 4; ++b) c->tile_set[p][b] = false;
+    return VECCHIA_OK;
+}
+
+int vecchia_set_timing(vecchia_ctx* c, int enable) {
+    if (!c) return VECCHIA_ERR_ARG;
+    c->timing = enable != 0;
+    return VECCHIA_OK;
+}
+
+int vecchia_genz_time_ms(const vecchia_ctx* c, double* ms) {
+    if (!c || !ms) return VECCHIA_ERR_ARG;
+    *ms = c->genz_ms;
+    return VECCHIA_OK;
+}
+
+}  // extern "C"

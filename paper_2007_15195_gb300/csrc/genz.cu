@@ -1,0 +1,613 @@
+// genz.cu -- the fused per-term kernel of the Vecchia log-CDF and the log-sum.
+//
+// One CTA takes one Vecchia term at a time (a site i of a problem):
+//   prologue (one warp, FP64): the block b = (N_i ascending, i) of
+//     Sec. 2.2 / Eq. (vecchia-cdf), its covariance from the covariance
+//     function (Sec. 3, Sec. 4.1), the Cholesky factor with lanes over rows;
+//   body (all warps): Genz's separation-of-variables recursion at the
+//     shifted lattice points, one lane per point, the numerator (d-dim) and
+//     denominator ((d-1)-dim, the leading block) sharing every sample;
+//   epilogue: per-shift lattice means num[i,s], den[i,s] in FP64.
+// The log-sum kernel then forms each term on the log scale and sums them in a
+// fixed order (Sec. 3.1), with the delta-method standard error over shifts.
+//
+// Genz's recursion for the d-dim CDF at u with Cholesky factor L (variables
+// v = 0..d-1, lattice coordinates t = 0..d-2):
+//   e_0 = Phi(u_0 / L_00)
+//   y_t = Phi^{-1}(w_t e_t),  w_t = tent(x_t) = 1 - |2 x_t - 1|
+//   e_{t+1} = Phi((u_{t+1} - sum_{j<=t} L_{t+1,j} y_j) / L_{t+1,t+1})
+//   numerator sample = e_0 ... e_{d-1},  denominator sample = e_0 ... e_{d-2}.
+// The partial sums u_v - sum_j L_vj y_j of all later variables are kept in
+// registers and updated right after each y_t (right-looking), so the loop over
+// t runs at run time with a fixed register array per lane.
+#include <cfloat>
+#include <climits>
+
+#include "vk_internal.h"
+
+namespace vk {
+namespace {
+
+constexpr int kMaxWarps = 16;
+constexpr int kMaxUnits = 64;  // shifts x slices handled by one CTA item
+
+__device__ __forceinline__ double cov_fn(int kind, double var, double range, double nu, double h) {
+    if (kind == VECCHIA_COV_EXPONENTIAL || nu == 0.5) return var * exp(-h / range);
+    if (nu == 1.5) {
+        const double a = 1.7320508075688772935 * h / range;
+        return var * (1.0 + a) * exp(-a);
+    }
+    const double a = 2.2360679774997896964 * h / range;
+    return var * (1.0 + a + a * a / 3.0) * exp(-a);
+}
+
+template <int DMAX, bool MIXED>
+struct GenzSmem {
+    using T = typename std::conditional<MIXED, float, double>::type;
+    double A[DMAX][DMAX + 1];  // covariance block, overwritten by its Cholesky factor
+    double bx[DMAX], by[DMAX], bu[DMAX];
+    double diag[DMAX];
+    __align__(16) T Lsh[DMAX][DMAX];  // Lsh[t][r] = L_{t+1+r,t}  (MIXED: / L_{t+1+r,t+1+r})
+    __align__(16) T up[DMAX];         // MIXED: u_v / L_vv;  FP64: u_v
+    uint32_t gl[DMAX];                // FP64: g_t;  MIXED: round(g_t 2^32 / N)
+    uint32_t dfix[MIXED ? kMaxS : 1][DMAX];
+    double part_num[kMaxUnits], part_den[kMaxUnits];
+    double e0, ec0;
+    int q, bad, flag;
+};
+
+// Phi(z) and 1 - Phi(z), the smaller one from the tail to full precision.
+__device__ __forceinline__ void phi_pair64(double z, double& e, double& ec) {
+    const double t = normcdf(-fabs(z));
+    e = (z < 0.0) ? t : 1.0 - t;
+    ec = (z < 0.0) ? 1.0 - t : t;
+}
+
+__device__ __forceinline__ void phi_pair32(float z, float& e, float& ec) {
+    const float t = normcdff(-fabsf(z));
+    e = (z < 0.0f) ? t : 1.0f - t;
+    ec = (z < 0.0f) ? 1.0f - t : t;
+}
+
+// Phi^{-1}(p) given p and q = 1 - p: from the smaller tail, clamped at 2^-1000.
+__device__ __forceinline__ double phiinv_pq64(double p, double q) {
+    const double lo = 9.3326361850321887899e-302;  // 2^-1000
+    const double pc = fmax(p, lo), qc = fmax(q, lo);
+    return (pc <= qc) ? normcdfinv(pc) : -normcdfinv(qc);
+}
+
+__device__ __forceinline__ float phiinv_pq32(float p, float q) {
+    const float r = fmaxf(fminf(p, q), FLT_MIN);
+    const float y = normcdfinvf(r);
+    return (p <= q) ? y : -y;
+}
+
+// 2^-E as a double (0 once below the normal range).
+__device__ __forceinline__ double pow2_neg(int E) {
+    return (E < 1022) ? __longlong_as_double((long long)(1023 - E) << 52) : 0.0;
+}
+
+template <int DMAX, int P>
+__device__ __forceinline__ void genz_points_mixed(const GenzSmem<DMAX, true>& sm, int q, int s,
+                                                  int64_t k_begin, int64_t k_end, double& acc_num,
+                                                  double& acc_den) {
+    constexpr int W = DMAX - 1;
+    const int lane = threadIdx.x & 31;
+    const uint32_t* dfs = sm.dfix[s];
+    for (int64_t kb = k_begin; kb < k_end; kb += 32 * P) {
+        float R[P][W];
+        float e[P], ec[P], g[P];
+        int E[P];
+        uint32_t kk[P];
+        bool valid[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int64_t k = kb + p * 32 + lane;
+            valid[p] = k < k_end;
+            kk[p] = (uint32_t)(valid[p] ? k : k_begin);
+#pragma unroll
+            for (int r = 0; r < W; ++r) R[p][r] = sm.up[1 + r];
+            e[p] = (float)sm.e0;
+            ec[p] = (float)sm.ec0;
+            g[p] = 1.0f;
+            E[p] = 0;
+        }
+        for (int t = 0; t < q; ++t) {
+            const float* Lrow = sm.Lsh[t];
+            const uint32_t G = sm.gl[t], Dt = dfs[t];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (t > 0) {  // g = e_1 ... e_t, exponent tracked so it never underflows
+                    g[p] *= e[p];
+                    if (g[p] < 0x1p-32f) {
+                        g[p] *= 0x1p32f;
+                        E[p] += 32;
+                    }
+                }
+                // lattice point in 32-bit fixed point, tent transform
+                const uint32_t X = kk[p] * G + Dt;
+                const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
+                const float w = __uint2float_rn(V) * 0x1p-31f;                // 1 - |2x - 1|
+                const float a = __uint2float_rn(0x80000000u - V) * 0x1p-31f;  // |2x - 1|
+                const float pp = w * e[p];
+                const float qq = fmaf(w, ec[p], a);
+                const float y = phiinv_pq32(pp, qq);
+                const float z = fmaf(-Lrow[0], y, R[p][0]);
+#pragma unroll
+                for (int r = 0; r + 1 < W; ++r) R[p][r] = fmaf(-Lrow[r + 1], y, R[p][r + 1]);
+                phi_pair32(z, e[p], ec[p]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (valid[p]) {
+                const double sc = pow2_neg(E[p]);
+                acc_den += (double)g[p] * sc;
+                acc_num += (double)(g[p] * e[p]) * sc;
+            }
+        }
+    }
+}
+
+template <int DMAX>
+__device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm, const ProbDev& P,
+                                                 int q, int s, int64_t k_begin, int64_t k_end,
+                                                 double& acc_num, double& acc_den) {
+    constexpr int W = DMAX - 1;
+    const int lane = threadIdx.x & 31;
+    const double* dl = P.delta + (int64_t)s * P.dim;
+    const uint64_t N = (uint64_t)P.N;
+    const double Nd = (double)P.N;
+    for (int64_t k = k_begin + lane; k < k_end; k += 32) {
+        double R[W];
+#pragma unroll
+        for (int r = 0; r < W; ++r) R[r] = sm.up[1 + r];
+        double e = sm.e0, ec = sm.ec0, f = 1.0;
+        for (int t = 0; t < q; ++t) {
+            f *= e;  // e_0 ... e_t
+            const uint64_t rr = ((uint64_t)k * (uint64_t)sm.gl[t]) % N;
+            double x = __dadd_rn((double)rr / Nd, dl[t]);
+            if (x >= 1.0) x -= 1.0;
+            const double a = fabs(__dsub_rn(__dmul_rn(2.0, x), 1.0));
+            const double w = __dsub_rn(1.0, a);
+            const double pp = __dmul_rn(w, e);
+            const double qq = __dadd_rn(a, __dmul_rn(w, ec));
+            const double y = phiinv_pq64(pp, qq);
+            const double* Lrow = sm.Lsh[t];
+            const double acc = fma(-Lrow[0], y, R[0]);
+#pragma unroll
+            for (int r = 0; r + 1 < W; ++r) R[r] = fma(-Lrow[r + 1], y, R[r + 1]);
+            phi_pair64(acc / sm.diag[t + 1], e, ec);
+        }
+        acc_den += f;
+        acc_num += f * e;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Work items: (problem, site, shift group).  A list of segments maps a flat
+// item index to them: segment k covers items [seg_prefix[k], seg_prefix[k+1])
+// = sites seg_base[k].y, ... of problem seg_base[k].x, each split into
+// `groups` shift groups (the group index varies fastest).  With an explicit
+// `items` list (the FP64 re-evaluation of flagged sites) an item is
+// (problem, site) with all shifts, and its count may live on the device.
+struct ItemSrc {
+    const int2* items;       // explicit (problem, site) items, or nullptr
+    const int* dev_count;    // device-side count for `items`, or nullptr
+    const int* seg_prefix;   // n_segs + 1 prefix sums of items
+    const int2* seg_base;    // (problem, first site) per segment
+    int n_segs;
+    int n_items;
+    int groups;              // shift groups per site (segment mode)
+};
+
+__device__ __forceinline__ void item_of(const ItemSrc& src, int it, int2& ps, int& grp) {
+    if (src.items) {
+        ps = src.items[it];
+        grp = 0;
+        return;
+    }
+    const int site_item = it / src.groups;
+    grp = it - site_item * src.groups;
+    int lo = 0, hi = src.n_segs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (src.seg_prefix[mid] <= site_item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    ps = make_int2(src.seg_base[lo].x, src.seg_base[lo].y + (site_item - src.seg_prefix[lo]));
+}
+
+template <int DMAX, int P, bool MIXED>
+__global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ probs, ItemSrc src,
+                                                   int slices, ProbResult* __restrict__ results,
+                                                   int* __restrict__ fallback_count,
+                                                   int2* __restrict__ fallback_items) {
+    __shared__ GenzSmem<DMAX, MIXED> sm;
+    using T = typename GenzSmem<DMAX, MIXED>::T;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int n_warps = blockDim.x >> 5;
+
+    const int n_run = src.dev_count ? min(*src.dev_count, src.n_items) : src.n_items;
+    for (int it = blockIdx.x; it < n_run; it += gridDim.x) {
+        int2 item;
+        int grp;
+        item_of(src, it, item, grp);
+        const ProbDev& Pd = probs[item.x];
+        const int64_t site = item.y;
+        const int m = Pd.m;
+        const int q = (int)((site < m) ? site : m);
+        const int d = q + 1;
+        const int S = Pd.S;
+        const int groups = src.items ? 1 : src.groups;
+        const int s_lo = (S * grp) / groups, s_hi = (S * (grp + 1)) / groups;
+
+        // ---- prologue: block, covariance, Cholesky (warp 0, FP64) ----
+        if (warp == 0) {
+            int idx = -1;
+            bool ok = true;
+            if (lane < d) {
+                idx = (lane < q) ? Pd.nbr[site * m + lane] : (int)site;
+                if (lane < q) ok = (idx >= 0) && (idx < site);
+            }
+            const int prev = __shfl_up_sync(0xffffffffu, idx, 1);
+            if (lane > 0 && lane < q && idx <= prev) ok = false;  // ascending (Sec. 2.2 block order)
+            const bool all_ok = __all_sync(0xffffffffu, ok);
+            if (all_ok && lane < d) {
+                sm.bx[lane] = Pd.sites[2 * (int64_t)idx];
+                sm.by[lane] = Pd.sites[2 * (int64_t)idx + 1];
+                sm.bu[lane] = Pd.u[idx];
+            }
+            __syncwarp();
+            int bad = all_ok ? 0 : 2;
+            if (!bad && lane < d) {
+                for (int c = 0; c <= lane; ++c) {
+                    const double dx = __dsub_rn(sm.bx[lane], sm.bx[c]);
+                    const double dy = __dsub_rn(sm.by[lane], sm.by[c]);
+                    const double h = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+                    double v = cov_fn(Pd.cov_kind, Pd.variance, Pd.range, Pd.nu, h);
+                    if (c == lane) v += Pd.nugget;
+                    sm.A[lane][c] = v;
+                }
+            }
+            __syncwarp();
+            // Cholesky, column by column; every entry's inner sum runs in
+            // ascending k with fma, as in the row-by-row definition.
+            for (int j = 0; j < d && !bad; ++j) {
+                bool piv_ok = true;
+                if (lane == j) {
+                    double s = sm.A[j][j];
+                    for (int k = 0; k < j; ++k) s = fma(-sm.A[j][k], sm.A[j][k], s);
+                    piv_ok = s > 0.0;
+                    sm.A[j][j] = sqrt(s);
+                }
+                if (!__shfl_sync(0xffffffffu, (int)piv_ok, j)) {
+                    bad = 1;
+                    break;
+                }
+                __syncwarp();
+                if (lane > j && lane < d) {
+                    double s = sm.A[lane][j];
+                    for (int k = 0; k < j; ++k) s = fma(-sm.A[lane][k], sm.A[j][k], s);
+                    sm.A[lane][j] = s / sm.A[j][j];
+                }
+                __syncwarp();
+            }
+            if (lane == 0) {
+                sm.bad = bad;
+                sm.q = q;
+                sm.flag = 0;
+                if (!bad) {
+                    const double z0 = sm.bu[0] / sm.A[0][0];
+                    phi_pair64(z0, sm.e0, sm.ec0);
+                }
+            }
+        }
+        __syncthreads();
+
+        if (!sm.bad) {
+            // ---- derived tables for the recursion ----
+            for (int x = threadIdx.x; x < DMAX * DMAX; x += blockDim.x) {
+                const int t = x / DMAX, r = x % DMAX, v = t + 1 + r;
+                T val = (T)0;
+                if (t < q && v < d) {
+                    if constexpr (MIXED)
+                        val = (T)(sm.A[v][t] / sm.A[v][v]);
+                    else
+                        val = sm.A[v][t];
+                }
+                sm.Lsh[t][r] = val;
+            }
+            for (int v = threadIdx.x; v < DMAX; v += blockDim.x) {
+                T val = (T)0;
+                if (v < d) {
+                    if constexpr (MIXED)
+                        val = (T)(sm.bu[v] / sm.A[v][v]);
+                    else
+                        val = sm.bu[v];
+                    sm.diag[v] = sm.A[v][v];
+                }
+                sm.up[v] = val;
+                if (v < q) sm.gl[v] = MIXED ? Pd.gfix[v] : Pd.g[v];
+            }
+            if constexpr (MIXED) {
+                for (int x = threadIdx.x; x < S * DMAX; x += blockDim.x) {
+                    const int s = x / DMAX, t = x % DMAX;
+                    sm.dfix[s][t] = (t < q) ? Pd.dfix[(int64_t)s * Pd.dim + t] : 0u;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- body: Genz recursion over shifts x lattice slices ----
+        const int units = (s_hi - s_lo) * slices;
+        if (!sm.bad && q > 0) {
+            for (int un = warp; un < units; un += n_warps) {
+                const int s = s_lo + un / slices, h = un % slices;
+                const int64_t k0 = (Pd.N * h) / slices, k1 = (Pd.N * (h + 1)) / slices;
+                double an = 0.0, ad = 0.0;
+                if constexpr (MIXED)
+                    genz_points_mixed<DMAX, P>(sm, q, s, k0, k1, an, ad);
+                else
+                    genz_points_fp64<DMAX>(sm, Pd, q, s, k0, k1, an, ad);
+                an = warp_sum(an);
+                ad = warp_sum(ad);
+                if (lane == 0) {
+                    sm.part_num[un] = an;
+                    sm.part_den[un] = ad;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- epilogue: per-shift means ----
+        for (int s = s_lo + threadIdx.x; s < s_hi; s += blockDim.x) {
+            const int un0 = (s - s_lo) * slices;
+            double vn, vd;
+            if (sm.bad) {
+                vn = vd = __longlong_as_double(0x7ff8000000000000LL);
+            } else if (q == 0) {
+                vn = sm.e0;
+                vd = 1.0;
+            } else {
+                double sn = 0.0, sd = 0.0;
+                for (int h = 0; h < slices; ++h) {
+                    sn += sm.part_num[un0 + h];
+                    sd += sm.part_den[un0 + h];
+                }
+                vn = sn / (double)Pd.N;
+                vd = sd / (double)Pd.N;
+                if constexpr (MIXED) {
+                    vn *= sm.e0;
+                    vd *= sm.e0;
+                    if (!(vn > 0.0) || !(vd > 0.0) || !isfinite(vn) || !isfinite(vd)) sm.flag = 1;
+                }
+            }
+            Pd.num[site * S + s] = vn;
+            Pd.den[site * S + s] = vd;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (sm.bad) {
+                atomicMin((unsigned long long*)&results[item.x].bad_site, (unsigned long long)site);
+                results[item.x].status = (sm.bad == 1) ? VECCHIA_ERR_NOT_PD : VECCHIA_ERR_ARG;
+            } else if (MIXED && sm.flag && fallback_items) {
+                const int pos = atomicAdd(fallback_count, 1);
+                fallback_items[pos] = item;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------- log-sum ------------------------------------
+
+constexpr int kSumThreads = 256;
+
+__device__ double block_sum(double v, double* red) {
+    const int tid = threadIdx.x;
+    red[tid] = v;
+    __syncthreads();
+    for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+        if (tid < o) red[tid] += red[tid + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kSumThreads) logsum_kernel(const ProbDev* __restrict__ probs,
+                                                             ProbResult* __restrict__ results,
+                                                             double* const* __restrict__ terms,
+                                                             double* __restrict__ means,
+                                                             const int64_t* __restrict__ means_off) {
+    __shared__ double red[kSumThreads];
+    const int pi = blockIdx.x;
+    const ProbDev& Pd = probs[pi];
+    const int64_t D = Pd.D;
+    const int S = Pd.S;
+    double* nb = means + means_off[pi];
+    double* db = nb + D;
+    double* tout = terms ? terms[pi] : nullptr;
+    double tsum = 0.0;
+    for (int64_t i = threadIdx.x; i < D; i += kSumThreads) {
+        double sn = 0.0, sd = 0.0;
+        for (int s = 0; s < S; ++s) {
+            sn += Pd.num[i * S + s];
+            sd += Pd.den[i * S + s];
+        }
+        const double a = sn / (double)S, b = sd / (double)S;
+        nb[i] = a;
+        db[i] = b;
+        const double T = log(a) - log(b);  // each term on the log scale (Sec. 3.1)
+        if (tout) tout[i] = T;
+        tsum += T;
+    }
+    const double log_p = block_sum(tsum, red);
+    double ss = 0.0;
+    for (int s = 0; s < S; ++s) {
+        double l = 0.0;
+        for (int64_t i = threadIdx.x; i < D; i += kSumThreads)
+            l += Pd.num[i * S + s] / nb[i] - Pd.den[i * S + s] / db[i];
+        const double ls = block_sum(l, red);
+        ss += ls * ls;
+    }
+    if (threadIdx.x == 0) {
+        ProbResult& R = results[pi];
+        R.log_p = log_p;
+        R.std_err = sqrt(ss / ((double)S * (double)(S - 1)));
+        if (R.status == VECCHIA_OK && !(isfinite(log_p) && isfinite(R.std_err)))
+            R.status = VECCHIA_ERR_NONFINITE;
+    }
+}
+
+__global__ void init_results_kernel(ProbResult* r, int n, int* fallback_count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        r[i].log_p = 0.0;
+        r[i].std_err = 0.0;
+        r[i].bad_site = LLONG_MAX;
+        r[i].status = VECCHIA_OK;
+        r[i].pad = 0;
+    }
+    if (i == 0 && fallback_count) *fallback_count = 0;
+}
+
+// ------------------------------- shifts -------------------------------------
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+__global__ void shifts_kernel(const uint64_t* __restrict__ seeds, const int32_t* __restrict__ Ss,
+                              const int64_t* __restrict__ off, int n_probs, int dim,
+                              double* __restrict__ delta, uint32_t* __restrict__ dfix) {
+    const int pi = blockIdx.y;
+    if (pi >= n_probs) return;
+    const int S = Ss[pi];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= S * dim) return;
+    const int s = x / dim, j = x % dim;
+    uint32_t c[4] = {(uint32_t)s, (uint32_t)j, 0x51A7u, 0u};
+    const uint64_t seed = seeds[pi];
+    philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    const uint64_t M = ((uint64_t)(c[0] >> 5) << 26) | (uint64_t)(c[1] >> 6);  // 53-bit integer
+    delta[off[pi] + x] = (double)M * 0x1p-53;
+    dfix[off[pi] + x] = (uint32_t)(M >> 21);
+}
+
+}  // namespace
+
+// ------------------------------- launchers ----------------------------------
+
+namespace {
+
+template <int DMAX, int P, bool MIXED>
+cudaError_t launch_one(const GenzTile& tile, const ProbDev* probs, const ItemSrc& src,
+                       ProbResult* results, int* fb_count, int2* fb_items, cudaStream_t st) {
+    auto kern = genz_kernel<DMAX, P, MIXED>;
+    static int per_sm[kMaxWarps + 1] = {0};
+    const int warps = tile.warps < 1 ? 1 : (tile.warps > kMaxWarps ? kMaxWarps : tile.warps);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (per_sm[warps] == 0) {
+        int b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, warps * 32, 0);
+        if (e != cudaSuccess) return e;
+        per_sm[warps] = b > 0 ? b : 1;
+    }
+    const int64_t cap = (int64_t)per_sm[warps] * device_sm_count(dev);
+    const int grid = (int)((src.n_items < cap) ? src.n_items : cap);
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, warps * 32, 0, st>>>(probs, src, tile.slices, results, fb_count, fb_items);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const ProbDev* probs,
+                        const int* seg_prefix, const int2* seg_base, int n_segs, int n_sites,
+                        ProbResult* results, int* fallback_count, int2* fallback_items, int max_S,
+                        cudaStream_t st) {
+    if (n_sites <= 0) return cudaSuccess;
+    GenzTile t = tile;
+    if (t.slices < 1) t.slices = 1;
+    if (t.groups < 1) t.groups = 1;
+    if (t.groups > max_S) t.groups = max_S;
+    const int per_group = (max_S + t.groups - 1) / t.groups;
+    while (t.slices > 1 && per_group * t.slices > kMaxUnits) --t.slices;
+    ItemSrc src{nullptr, nullptr, seg_prefix, seg_base, n_segs, n_sites * t.groups, t.groups};
+#define VK_CASE(DM)                                                                              \
+    case DM / 8 - 1:                                                                             \
+        if (!mixed) return launch_one<DM, 1, false>(t, probs, src, results, nullptr, nullptr, st); \
+        if (t.points >= 4)                                                                       \
+            return launch_one<DM, 4, true>(t, probs, src, results, fallback_count, fallback_items, st); \
+        if (t.points == 2)                                                                       \
+            return launch_one<DM, 2, true>(t, probs, src, results, fallback_count, fallback_items, st); \
+        return launch_one<DM, 1, true>(t, probs, src, results, fallback_count, fallback_items, st);
+    switch (bucket) {
+        VK_CASE(8)
+        VK_CASE(16)
+        VK_CASE(24)
+        VK_CASE(32)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef VK_CASE
+}
+
+cudaError_t launch_genz_fallback(const ProbDev* probs, const int* fallback_count,
+                                 const int2* fallback_items, int capacity, ProbResult* results,
+                                 cudaStream_t st) {
+    if (capacity <= 0) return cudaSuccess;
+    GenzTile t{4, 1, 1, 1};
+    ItemSrc src{fallback_items, fallback_count, nullptr, nullptr, 0, capacity, 1};
+    return launch_one<32, 1, false>(t, probs, src, results, nullptr, nullptr, st);
+}
+
+cudaError_t launch_logsum(const ProbDev* probs, int n_probs, ProbResult* results,
+                          double* const* terms, double* scratch_means, const int64_t* means_off,
+                          cudaStream_t st) {
+    if (n_probs <= 0) return cudaSuccess;
+    logsum_kernel<<<n_probs, kSumThreads, 0, st>>>(probs, results, terms, scratch_means, means_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shifts(const uint64_t* seeds, const int32_t* S, const int64_t* out_off,
+                          int n_probs, int dim, double* delta, uint32_t* dfix, cudaStream_t st) {
+    if (n_probs <= 0 || dim <= 0) return cudaSuccess;
+    const int per = kMaxS * dim;
+    dim3 grid((per + 127) / 128, n_probs);
+    shifts_kernel<<<grid, 128, 0, st>>>(seeds, S, out_off, n_probs, dim, delta, dfix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_results(ProbResult* results, int n, int* fallback_count, cudaStream_t st) {
+    const int nn = n > 1 ? n : 1;
+    init_results_kernel<<<(nn + 255) / 256, 256, 0, st>>>(results, n, fallback_count);
+    return cudaGetLastError();
+}
+
+}  // namespace vk
