@@ -173,6 +173,13 @@ int vecchia_set_timing(vecchia_ctx* ctx, int enable);
 /* Milliseconds between those events in the last call with timing on. */
 int vecchia_genz_time_ms(const vecchia_ctx* ctx, double* ms);
 
+/* Diagnostic: the FP32 special functions of the mixed path on n values (x and
+ * out device arrays of float): which = 0: Phi(x); 1: 1 - Phi(x); 2: log2 Phi(x)
+ * for x < -9 (NaN otherwise); 3: Phi^{-1}(x), x in (0, 1); 4: Phi^{-1}(2^x) for
+ * x < -64.  These are the maps of Genz's separation of variables (Sec. 2.2)
+ * in the precision the mixed path evaluates them. */
+int vecchia_eval_special(vecchia_ctx* ctx, int which, const float* x, int64_t n, float* out);
+
 /* Ordered index of the site whose block failed in the last call (or -1). */
 int64_t vecchia_last_error_site(const vecchia_ctx* ctx);
 

@@ -87,6 +87,7 @@ def lib():
         L.vecchia_set_tile.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
         L.vecchia_reset_tiles.argtypes = [_vp]
         L.vecchia_set_timing.argtypes = [_vp, C.c_int]
+        L.vecchia_eval_special.argtypes = [_vp, C.c_int, _vp, C.c_int64, _vp]
         L.vecchia_genz_time_ms.argtypes = [_vp, C.POINTER(C.c_double)]
         _lib = L
     return _lib
@@ -298,6 +299,15 @@ def vecchia_set_tile(ctx, precision, bucket, warps, points, slices, groups):
 
 def vecchia_reset_tiles(ctx):
     _check(lib().vecchia_reset_tiles(ctx.handle), "vecchia_reset_tiles", ctx)
+
+
+def vecchia_eval_special(ctx, which, x):
+    """FP32 special functions of the mixed path on a CUDA float32 tensor (diagnostic)."""
+    xx = x.to(torch.float32).contiguous()
+    out = torch.empty_like(xx)
+    _check(lib().vecchia_eval_special(ctx.handle, int(which), _ptr(xx), xx.numel(), _ptr(out)),
+           "vecchia_eval_special", ctx)
+    return out
 
 
 def vecchia_set_timing(ctx, enable=True):

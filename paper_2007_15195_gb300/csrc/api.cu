@@ -259,13 +259,17 @@ uint32_t* lattice_for(vecchia_ctx* c, int64_t N) {
     return d;
 }
 
+// Built-in tile: 4 warps, one point per lane, and enough shift groups (a power
+// of two, so that S = 2^k splits evenly) for ~4096 CTA items.
 GenzTile default_tile(bool mixed, int64_t total_sites, int max_S) {
     GenzTile t;
     t.warps = 4;
-    t.points = mixed ? 2 : 1;
+    t.points = 1;
     t.slices = 1;
-    int64_t g = (6144 + total_sites - 1) / std::max<int64_t>(total_sites, 1);
-    t.groups = (int)std::min<int64_t>(std::max<int64_t>(g, 1), max_S);
+    int g = 1;
+    while (g < max_S && (int64_t)g * total_sites < 4096) g *= 2;
+    t.groups = g;
+    (void)mixed;
     return t;
 }
 
@@ -855,6 +859,20 @@ int vecchia_reset_tiles(vecchia_ctx* c) {
     if (!c) return VECCHIA_ERR_ARG;
     for (int p = 0; p < 2; ++p)
         for (int b = 0; b < 4; ++b) c->tile_set[p][b] = false;
+    return VECCHIA_OK;
+}
+
+int vecchia_eval_special(vecchia_ctx* c, int which, const float* x, int64_t n, float* out) {
+    if (!c || which < 0 || which > 4 || n < 0 || (n > 0 && (!x || !out))) return VECCHIA_ERR_ARG;
+    if (n == 0) return VECCHIA_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    if (!is_device_ptr(x) || !is_device_ptr(out)) return VECCHIA_ERR_ARG;
+    cudaError_t e = vk::launch_eval_special(which, x, n, out, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
     return VECCHIA_OK;
 }
 

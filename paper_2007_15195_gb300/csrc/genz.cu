@@ -23,6 +23,7 @@
 #include <cfloat>
 #include <climits>
 
+#include "special_f32.h"
 #include "vk_internal.h"
 
 namespace vk {
@@ -47,12 +48,20 @@ struct GenzSmem {
     double A[DMAX][DMAX + 1];  // covariance block, overwritten by its Cholesky factor
     double bx[DMAX], by[DMAX], bu[DMAX];
     double diag[DMAX];
-    __align__(16) T Lsh[DMAX][DMAX];  // Lsh[t][r] = L_{t+1+r,t}  (MIXED: / L_{t+1+r,t+1+r})
-    __align__(16) T up[DMAX];         // MIXED: u_v / L_vv;  FP64: u_v
-    uint32_t gl[DMAX];                // FP64: g_t;  MIXED: round(g_t 2^32 / N)
+    // Recursion tables, step t (lattice coordinate t, variable t + 1 next):
+    //   Lz[t]      = L_{t+1,t}          coefficient of y_t in variable t+1
+    //   Lup[t][r]  = L_{t+2+r,t}        coefficients of y_t in the later variables
+    // MIXED divides each row v by L_vv (so the conditional mean is already
+    // standardised); FP64 keeps them unscaled and divides by L_vv, as the
+    // row-by-row definition does.
+    __align__(16) T Lup[DMAX][DMAX];
+    __align__(16) T Lz[DMAX];
+    __align__(16) T up[DMAX];  // MIXED: u_v / L_vv;  FP64: u_v
+    uint32_t gl[DMAX];         // FP64: g_t;  MIXED: round(g_t 2^32 / N)
     uint32_t dfix[MIXED ? kMaxS : 1][DMAX];
     double part_num[kMaxUnits], part_den[kMaxUnits];
     double e0, ec0;
+    float le2_0;  // log2 e0 when e0 < 2^-64 (mixed path)
     int q, bad, flag;
 };
 
@@ -63,12 +72,6 @@ __device__ __forceinline__ void phi_pair64(double z, double& e, double& ec) {
     ec = (z < 0.0) ? 1.0 - t : t;
 }
 
-__device__ __forceinline__ void phi_pair32(float z, float& e, float& ec) {
-    const float t = normcdff(-fabsf(z));
-    e = (z < 0.0f) ? t : 1.0f - t;
-    ec = (z < 0.0f) ? 1.0f - t : t;
-}
-
 // Phi^{-1}(p) given p and q = 1 - p: from the smaller tail, clamped at 2^-1000.
 __device__ __forceinline__ double phiinv_pq64(double p, double q) {
     const double lo = 9.3326361850321887899e-302;  // 2^-1000
@@ -76,92 +79,148 @@ __device__ __forceinline__ double phiinv_pq64(double p, double q) {
     return (pc <= qc) ? normcdfinv(pc) : -normcdfinv(qc);
 }
 
-__device__ __forceinline__ float phiinv_pq32(float p, float q) {
-    const float r = fmaxf(fminf(p, q), FLT_MIN);
-    const float y = normcdfinvf(r);
-    return (p <= q) ? y : -y;
-}
-
 // 2^-E as a double (0 once below the normal range).
 __device__ __forceinline__ double pow2_neg(int E) {
     return (E < 1022) ? __longlong_as_double((long long)(1023 - E) << 52) : 0.0;
+}
+
+// ------------------------ mixed (FP32 integrand) path ------------------------
+// Per lane and point: the standardised partial sums R of the later variables,
+// the current conditional probability e (and 1 - e, and log2 e once e is below
+// 2^-64), and the running product g 2^-E of e_1 .. e_t (e_0 is factored out
+// and applied in FP64), its exponent tracked so it never underflows.
+
+template <int DMAX, int P>
+struct MixedLanes {
+    float R[P][DMAX - 1];
+    float e[P], ec[P], le2[P], g[P];
+    int E[P];
+    bool tiny[P];
+    uint32_t kk[P];
+};
+
+__device__ __forceinline__ void scale_by(float& g, int& E, float v) {
+    g *= v;
+    if (g < 0x1p-32f) {
+        g *= 0x1p32f;
+        E += 32;
+    }
+}
+
+// g 2^-E times 2^l2 (l2 << 0), kept normal
+__device__ __forceinline__ void scale_by_log2(float& g, int& E, float l2) {
+    const float k = floorf(l2);
+    g *= special::ex2(l2 - k);
+    E -= (int)k;
+    if (g < 0x1p-32f) {
+        g *= 0x1p32f;
+        E += 32;
+    }
+}
+
+// Steps t0 <= t < t1 with update width W: each step needs q - t - 1 <= W.
+template <int DMAX, int P, int W>
+__device__ __forceinline__ void mixed_steps(const GenzSmem<DMAX, true>& sm, const uint32_t* dfs,
+                                            int t0, int t1, MixedLanes<DMAX, P>& L) {
+    for (int t = t0; t < t1; ++t) {
+        const float* lup = sm.Lup[t];
+        const float lz = sm.Lz[t];
+        const uint32_t G = sm.gl[t], Dt = dfs[t];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (t > 0) {  // g *= e_t
+                if (!L.tiny[p])
+                    scale_by(L.g[p], L.E[p], L.e[p]);
+                else
+                    scale_by_log2(L.g[p], L.E[p], L.le2[p]);
+            }
+            // lattice coordinate in 32-bit fixed point, tent transform w = 1 - |2x - 1|
+            const uint32_t X = L.kk[p] * G + Dt;
+            const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
+            const float w = __uint2float_rn(V) * 0x1p-31f;
+            float y;
+            if (!L.tiny[p]) {
+                const float a = __uint2float_rn(0x80000000u - V) * 0x1p-31f;  // |2x - 1|
+                y = special::phiinv_pq(w * L.e[p], fmaf(w, L.ec[p], a));
+            } else {  // w e_t below 2^-64: from log2(w e_t)
+                y = special::phiinv_log2(special::lg2(w) + L.le2[p]);
+            }
+            const float z = fmaf(-lz, y, L.R[p][0]);
+#pragma unroll
+            for (int r = 0; r < W; ++r) L.R[p][r] = fmaf(-lup[r], y, L.R[p][r + 1]);
+            special::phi_pair(z, L.e[p], L.ec[p], L.tiny[p], L.le2[p]);
+        }
+    }
+}
+
+template <int DMAX, int P, int W>
+__device__ __forceinline__ void mixed_phases(const GenzSmem<DMAX, true>& sm, const uint32_t* dfs,
+                                             int t, int q, MixedLanes<DMAX, P>& L) {
+    constexpr int WN = W - 8;
+    const int t_end = (WN > 0) ? max(t, min(q, q - 1 - WN)) : q;
+    mixed_steps<DMAX, P, W>(sm, dfs, t, t_end, L);
+    if constexpr (WN > 0) mixed_phases<DMAX, P, WN>(sm, dfs, t_end, q, L);
 }
 
 template <int DMAX, int P>
 __device__ __forceinline__ void genz_points_mixed(const GenzSmem<DMAX, true>& sm, int q, int s,
                                                   int64_t k_begin, int64_t k_end, double& acc_num,
                                                   double& acc_den) {
-    constexpr int W = DMAX - 1;
+    constexpr int W0 = (DMAX - 2 > 0) ? DMAX - 2 : 1;
     const int lane = threadIdx.x & 31;
     const uint32_t* dfs = sm.dfix[s];
+    const float e0f = (float)sm.e0, ec0f = (float)sm.ec0;
+    const bool tiny0 = sm.e0 < 0x1p-64;
     for (int64_t kb = k_begin; kb < k_end; kb += 32 * P) {
-        float R[P][W];
-        float e[P], ec[P], g[P];
-        int E[P];
-        uint32_t kk[P];
+        MixedLanes<DMAX, P> L;
         bool valid[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const int64_t k = kb + p * 32 + lane;
             valid[p] = k < k_end;
-            kk[p] = (uint32_t)(valid[p] ? k : k_begin);
+            L.kk[p] = (uint32_t)(valid[p] ? k : k_begin);
 #pragma unroll
-            for (int r = 0; r < W; ++r) R[p][r] = sm.up[1 + r];
-            e[p] = (float)sm.e0;
-            ec[p] = (float)sm.ec0;
-            g[p] = 1.0f;
-            E[p] = 0;
+            for (int r = 0; r < DMAX - 1; ++r) L.R[p][r] = sm.up[1 + r];
+            L.e[p] = e0f;
+            L.ec[p] = ec0f;
+            L.tiny[p] = tiny0;
+            L.le2[p] = sm.le2_0;
+            L.g[p] = 1.0f;
+            L.E[p] = 0;
         }
-        for (int t = 0; t < q; ++t) {
-            const float* Lrow = sm.Lsh[t];
-            const uint32_t G = sm.gl[t], Dt = dfs[t];
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (t > 0) {  // g = e_1 ... e_t, exponent tracked so it never underflows
-                    g[p] *= e[p];
-                    if (g[p] < 0x1p-32f) {
-                        g[p] *= 0x1p32f;
-                        E[p] += 32;
-                    }
-                }
-                // lattice point in 32-bit fixed point, tent transform
-                const uint32_t X = kk[p] * G + Dt;
-                const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
-                const float w = __uint2float_rn(V) * 0x1p-31f;                // 1 - |2x - 1|
-                const float a = __uint2float_rn(0x80000000u - V) * 0x1p-31f;  // |2x - 1|
-                const float pp = w * e[p];
-                const float qq = fmaf(w, ec[p], a);
-                const float y = phiinv_pq32(pp, qq);
-                const float z = fmaf(-Lrow[0], y, R[p][0]);
-#pragma unroll
-                for (int r = 0; r + 1 < W; ++r) R[p][r] = fmaf(-Lrow[r + 1], y, R[p][r + 1]);
-                phi_pair32(z, e[p], ec[p]);
-            }
-        }
+        mixed_phases<DMAX, P, W0>(sm, dfs, 0, q, L);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (valid[p]) {
-                const double sc = pow2_neg(E[p]);
-                acc_den += (double)g[p] * sc;
-                acc_num += (double)(g[p] * e[p]) * sc;
+                const double den = (double)L.g[p] * pow2_neg(L.E[p]);
+                float gn = L.g[p];
+                int En = L.E[p];
+                if (!L.tiny[p])
+                    scale_by(gn, En, L.e[p]);
+                else
+                    scale_by_log2(gn, En, L.le2[p]);
+                acc_den += den;
+                acc_num += (double)gn * pow2_neg(En);
             }
         }
     }
 }
 
+// ------------------------------- FP64 path ---------------------------------
+
 template <int DMAX>
 __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm, const ProbDev& P,
                                                  int q, int s, int64_t k_begin, int64_t k_end,
                                                  double& acc_num, double& acc_den) {
-    constexpr int W = DMAX - 1;
+    constexpr int W = DMAX - 2;
     const int lane = threadIdx.x & 31;
     const double* dl = P.delta + (int64_t)s * P.dim;
     const uint64_t N = (uint64_t)P.N;
     const double Nd = (double)P.N;
     for (int64_t k = k_begin + lane; k < k_end; k += 32) {
-        double R[W];
+        double R[DMAX - 1];
 #pragma unroll
-        for (int r = 0; r < W; ++r) R[r] = sm.up[1 + r];
+        for (int r = 0; r < DMAX - 1; ++r) R[r] = sm.up[1 + r];
         double e = sm.e0, ec = sm.ec0, f = 1.0;
         for (int t = 0; t < q; ++t) {
             f *= e;  // e_0 ... e_t
@@ -173,10 +232,10 @@ __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm
             const double pp = __dmul_rn(w, e);
             const double qq = __dadd_rn(a, __dmul_rn(w, ec));
             const double y = phiinv_pq64(pp, qq);
-            const double* Lrow = sm.Lsh[t];
-            const double acc = fma(-Lrow[0], y, R[0]);
+            const double* lup = sm.Lup[t];
+            const double acc = fma(-sm.Lz[t], y, R[0]);
 #pragma unroll
-            for (int r = 0; r + 1 < W; ++r) R[r] = fma(-Lrow[r + 1], y, R[r + 1]);
+            for (int r = 0; r < W; ++r) R[r] = fma(-lup[r], y, R[r + 1]);
             phi_pair64(acc / sm.diag[t + 1], e, ec);
         }
         acc_den += f;
@@ -308,6 +367,7 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
                 if (!bad) {
                     const double z0 = sm.bu[0] / sm.A[0][0];
                     phi_pair64(z0, sm.e0, sm.ec0);
+                    sm.le2_0 = (sm.e0 < 0x1p-64) ? (float)log2(sm.e0) : 0.0f;
                 }
             }
         }
@@ -316,7 +376,7 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
         if (!sm.bad) {
             // ---- derived tables for the recursion ----
             for (int x = threadIdx.x; x < DMAX * DMAX; x += blockDim.x) {
-                const int t = x / DMAX, r = x % DMAX, v = t + 1 + r;
+                const int t = x / DMAX, r = x % DMAX, v = t + 2 + r;
                 T val = (T)0;
                 if (t < q && v < d) {
                     if constexpr (MIXED)
@@ -324,10 +384,10 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
                     else
                         val = sm.A[v][t];
                 }
-                sm.Lsh[t][r] = val;
+                sm.Lup[t][r] = val;
             }
             for (int v = threadIdx.x; v < DMAX; v += blockDim.x) {
-                T val = (T)0;
+                T val = (T)0, lz = (T)0;
                 if (v < d) {
                     if constexpr (MIXED)
                         val = (T)(sm.bu[v] / sm.A[v][v]);
@@ -335,7 +395,14 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
                         val = sm.bu[v];
                     sm.diag[v] = sm.A[v][v];
                 }
+                if (v < q) {
+                    if constexpr (MIXED)
+                        lz = (T)(sm.A[v + 1][v] / sm.A[v + 1][v + 1]);
+                    else
+                        lz = sm.A[v + 1][v];
+                }
                 sm.up[v] = val;
+                sm.Lz[v] = lz;
                 if (v < q) sm.gl[v] = MIXED ? Pd.gfix[v] : Pd.g[v];
             }
             if constexpr (MIXED) {
@@ -518,7 +585,31 @@ __global__ void shifts_kernel(const uint64_t* __restrict__ seeds, const int32_t*
     dfix[off[pi] + x] = (uint32_t)(M >> 21);
 }
 
+__global__ void eval_special_kernel(int which, const float* __restrict__ x, int64_t n,
+                                    float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = x[i];
+    float e, ec, le2 = 0.0f, r = 0.0f;
+    bool tiny;
+    switch (which) {
+        case 0: special::phi_pair(v, e, ec, tiny, le2); r = e; break;
+        case 1: special::phi_pair(v, e, ec, tiny, le2); r = ec; break;
+        case 2: special::phi_pair(v, e, ec, tiny, le2); r = tiny ? le2 : NAN; break;
+        case 3: r = special::phiinv_pq(v, 1.0f - v); break;
+        case 4: r = special::phiinv_log2(v); break;
+        default: r = NAN;
+    }
+    out[i] = r;
+}
+
 }  // namespace
+
+cudaError_t launch_eval_special(int which, const float* x, int64_t n, float* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    eval_special_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(which, x, n, out);
+    return cudaGetLastError();
+}
 
 // ------------------------------- launchers ----------------------------------
 

@@ -1,0 +1,98 @@
+// special_f32.h -- FP32 normal CDF and quantile for the mixed Genz kernel,
+// with a log-space path for probabilities below 2^-64.
+//
+// Phi of the lower tail (Numerical Recipes "erfcc" form, own coefficients):
+//     Phi(-z) = t 2^(a),  t = 1/(1 + z/(2 sqrt 2)),  a = -z^2 log2(e)/2 + P(t),  z >= 0.
+// log2 Phi(-z) = log2 t + a is available without underflow.
+// Phi^{-1} of the lower tail (M. Giles' erfinv form, own coefficients):
+//     Phi^{-1}(r) = -sqrt(2) y f(w),  y = 1 - 2r,  w = -ln(4 r (1 - r)).
+// From a log-probability (r < 2^-64): w = -(ln 4 + ln r), y = 1.
+// Coefficients: special_f32.cuh (generated by fit_special.py).
+#pragma once
+
+#include "special_f32.cuh"
+
+namespace vk {
+namespace special {
+
+constexpr float kLn2 = 0.693147180559945309f;
+constexpr float kLn4 = 1.38629436111989062f;
+constexpr float kSqrt2 = 1.41421356237309505f;
+constexpr float kTinyZ = -9.0f;   // Phi(-9) ~ 2^-62.5: below, carry log2 Phi instead
+constexpr float kFloor = 1.17549435e-38f;  // smallest normal float: clamp of r
+
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int N>
+__device__ __forceinline__ float horner(const float (&c)[N], float u) {
+    float acc = c[N - 1];
+#pragma unroll
+    for (int k = N - 2; k >= 0; --k) acc = fmaf(acc, u, c[k]);
+    return acc;
+}
+
+// Phi(z) and 1 - Phi(z); for z < kTinyZ also log2 Phi(z) (then e may be 0).
+__device__ __forceinline__ void phi_pair(float z, float& e, float& ec, bool& tiny, float& le2) {
+    const float az = fminf(fabsf(z), kZmax);
+    const float t = rcp(fmaf(az, kKt, 1.0f));
+    const float a = fmaf(az * (-0.5f * kLog2e), az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float tail = t * ex2(a);  // Phi(-|z|)
+    const bool neg = z < 0.0f;
+    e = neg ? tail : 1.0f - tail;
+    ec = neg ? 1.0f - tail : tail;
+    tiny = z < kTinyZ;
+    if (tiny) le2 = lg2(t) + a;
+}
+
+// f(w) = erfinv(y)/y for w >= 5 (sqrt(w) pieces).
+__device__ __forceinline__ float finv_tail(float w) {
+    const float s = sqrt_approx(w);
+    if (s < 6.0f) return horner(kINV2C, fmaf(s, kINV2A, kINV2B));
+    if (s < 11.4017543f) return horner(kINV3C, fmaf(s, kINV3A, kINV3B));
+    return horner(kINV4C, fmaf(fminf(s, 26.4575131f), kINV4A, kINV4B));
+}
+
+// Phi^{-1}(p) given p and q = 1 - p (both >= 0): from the smaller tail.
+__device__ __forceinline__ float phiinv_pq(float p, float q) {
+    const float r = fmaxf(fminf(p, q), kFloor);
+    const float o = fmaxf(p, q);
+    const float w = -kLn2 * lg2(4.0f * r * o);
+    float f;
+    if (w < 5.0f)
+        f = horner(kINV1C, fmaf(w, kINV1A, kINV1B));
+    else
+        f = finv_tail(w);
+    const float x = kSqrt2 * (o - r) * f;  // -Phi^{-1}(r) >= 0
+    return (p <= q) ? -x : x;
+}
+
+// Phi^{-1}(r) for r = 2^lr2 < 2^-64 (log2 input).
+__device__ __forceinline__ float phiinv_log2(float lr2) {
+    const float w = -(kLn4 + kLn2 * fmaxf(lr2, -1009.0f));
+    return -kSqrt2 * finv_tail(w);
+}
+
+}  // namespace special
+}  // namespace vk

@@ -94,6 +94,9 @@ cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void
 cudaError_t launch_gather(const int32_t* perm, const double* sites, const double* u, int64_t D,
                           double* sites_out, double* u_out, int* bad, cudaStream_t st);
 
+// The FP32 special functions of the mixed path on n device values (diagnostic).
+cudaError_t launch_eval_special(int which, const float* x, int64_t n, float* out, cudaStream_t st);
+
 int device_sm_count(int device);
 
 }  // namespace vk
