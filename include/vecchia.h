@@ -159,8 +159,9 @@ int vecchia_lattice(int64_t N, int dim, uint32_t* g);
 int vecchia_shifts(uint64_t seed, int S, int dim, double* delta);
 
 /* Launch tile of the fused Genz kernel for one precision and block bucket
- * (bucket b holds problems with m + 1 <= 8, 16, 24, 32 for b = 0..3; -1 = all):
- * warps per CTA (1..16), points per lane per pass (1, 2, 4; FP64 uses 1),
+ * (bucket b holds problems with m + 1 <= 9, 13, 17, 21, 25, 29, 32 for
+ * b = 0..6; -1 = all): warps per CTA (1..16), points per lane per pass (1 or
+ * 2; FP64 uses 1),
  * lattice slices per shift spread over a CTA's warps (>= 1), shift groups per
  * site spread over CTAs (1..VECCHIA_MAX_S).  Tiles change only the launch
  * shape; results are identical up to the order of the final FP64 sums. */

@@ -88,7 +88,6 @@ def lib():
         L.vecchia_reset_tiles.argtypes = [_vp]
         L.vecchia_set_timing.argtypes = [_vp, C.c_int]
         L.vecchia_eval_special.argtypes = [_vp, C.c_int, _vp, C.c_int64, _vp]
-        L.vecchia_genz_time_ms.argtypes = [_vp, C.POINTER(C.c_double)]
         _lib = L
     return _lib
 

@@ -21,8 +21,8 @@ struct vecchia_ctx {
     size_t host_stage_cap = 0;
     std::map<int64_t, uint32_t*> lattice_dev;  // N -> device [g(32) | gfix(32)]
     int64_t last_error_site = -1;
-    vk::GenzTile tile[2][4];
-    bool tile_set[2][4] = {{false}};
+    vk::GenzTile tile[2][vk::kNumBuckets];
+    bool tile_set[2][vk::kNumBuckets] = {{false}};
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double genz_ms = 0.0;
@@ -315,9 +315,10 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
 
     // buckets and totals
     int64_t total_sites = 0, total_ds = 0, fb_cap = 0;
-    int max_S[4] = {0, 0, 0, 0};
-    int64_t bucket_sites[4] = {0, 0, 0, 0};
-    int bucket_segs[4] = {0, 0, 0, 0};
+    constexpr int NB = vk::kNumBuckets;
+    int max_S[NB] = {0};
+    int64_t bucket_sites[NB] = {0};
+    int bucket_segs[NB] = {0};
     std::vector<int> bucket_of(n, -1);
     for (int i = 0; i < n; ++i) {
         if (!ok[i]) continue;
@@ -329,9 +330,9 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
         total_sites += probs[i].D;
         total_ds += probs[i].D * probs[i].S;
     }
-    GenzTile tiles[4];
+    GenzTile tiles[NB];
     int max_groups = 1;
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < NB; ++b) {
         tiles[b] = c->tile_set[mixed][b] ? c->tile[mixed][b] : default_tile(mixed, total_sites, std::max(max_S[b], 2));
         max_groups = std::max(max_groups, tiles[b].groups);
     }
@@ -364,8 +365,14 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
         o_den[i] = dv.off;
         dv.take<double>((size_t)p.D * p.S);
     }
+    int64_t logsum_doubles = 0, max_slices = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!ok[i]) continue;
+        logsum_doubles += vk::logsum_scratch(probs[i].D, probs[i].S);
+        max_slices = std::max(max_slices, vk::logsum_slices(probs[i].D));
+    }
     const size_t o_means = dv.off;
-    dv.take<double>(2 * total_sites);
+    dv.take<double>(logsum_doubles);
     const size_t o_delta = dv.off;
     dv.take<double>((size_t)n * vk::kMaxS * kDim);
     const size_t o_dfix = dv.off;
@@ -394,8 +401,8 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
     hb.take<int64_t>(n);
     const size_t b_tptr = hb.off;
     hb.take<double*>(n);
-    size_t b_segp[4], b_segb[4];
-    for (int b = 0; b < 4; ++b) {
+    size_t b_segp[NB], b_segb[NB];
+    for (int b = 0; b < NB; ++b) {
         b_segp[b] = hb.off;
         hb.take<int>(bucket_segs[b] + 1);
         b_segb[b] = hb.off;
@@ -451,9 +458,9 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
         d.S = p.S;
         d.dim = kDim;
         if (terms) htp[i] = terms_host ? (double*)(A + o_terms_out) : terms;
-        moff += 2 * p.D;
+        moff += vk::logsum_scratch(p.D, p.S);
     }
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < NB; ++b) {
         int* sp = (int*)(H + b_segp[b]);
         int2* sb = (int2*)(H + b_segb[b]);
         int k = 0, run = 0;
@@ -492,7 +499,7 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
                               (uint32_t*)(A + o_dfix), s);
     if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev0, s);
     // largest blocks first
-    for (int b = 3; b >= 0 && e == cudaSuccess; --b) {
+    for (int b = NB - 1; b >= 0 && e == cudaSuccess; --b) {
         if (!bucket_sites[b]) continue;
         e = vk::launch_genz(b, mixed, tiles[b], probs_d, (const int*)(blob_dev + b_segp[b]),
                             (const int2*)(blob_dev + b_segb[b]), bucket_segs[b], (int)bucket_sites[b],
@@ -502,7 +509,8 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
     if (mixed && e == cudaSuccess)
         e = vk::launch_genz_fallback(probs_d, fbc, fbi, (int)fb_cap, res_d, s);
     if (e == cudaSuccess)
-        e = vk::launch_logsum(probs_d, n, res_d, terms ? (double* const*)(blob_dev + b_tptr) : nullptr,
+        e = vk::launch_logsum(probs_d, n, (int)max_slices, res_d,
+                              terms ? (double* const*)(blob_dev + b_tptr) : nullptr,
                               (double*)(A + o_means), (const int64_t*)(blob_dev + b_moff), s);
     ProbResult* hres = (ProbResult*)(H + b_results);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hres, res_d, sizeof(ProbResult) * n, cudaMemcpyDeviceToHost, s);
@@ -842,12 +850,13 @@ int vecchia_log_cdf_batch(vecchia_ctx* c, const vecchia_problem* probs, int n_pr
 
 int vecchia_set_tile(vecchia_ctx* c, int precision, int bucket, int warps, int points, int slices,
                      int groups) {
-    if (!c || (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) || bucket < -1 || bucket > 3)
+    if (!c || (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) || bucket < -1 ||
+        bucket >= vk::kNumBuckets)
         return VECCHIA_ERR_ARG;
-    if (warps < 1 || warps > 16 || (points != 1 && points != 2 && points != 4) || slices < 1 ||
+    if (warps < 1 || warps > 16 || (points != 1 && points != 2) || slices < 1 ||
         groups < 1 || groups > VECCHIA_MAX_S)
         return VECCHIA_ERR_ARG;
-    const int b0 = bucket < 0 ? 0 : bucket, b1 = bucket < 0 ? 3 : bucket;
+    const int b0 = bucket < 0 ? 0 : bucket, b1 = bucket < 0 ? vk::kNumBuckets - 1 : bucket;
     for (int b = b0; b <= b1; ++b) {
         c->tile[precision][b] = vk::GenzTile{warps, precision == VECCHIA_FP64 ? 1 : points, slices, groups};
         c->tile_set[precision][b] = true;
@@ -858,7 +867,7 @@ int vecchia_set_tile(vecchia_ctx* c, int precision, int bucket, int warps, int p
 int vecchia_reset_tiles(vecchia_ctx* c) {
     if (!c) return VECCHIA_ERR_ARG;
     for (int p = 0; p < 2; ++p)
-        for (int b = 0; b < 4; ++b) c->tile_set[p][b] = false;
+        for (int b = 0; b < vk::kNumBuckets; ++b) c->tile_set[p][b] = false;
     return VECCHIA_OK;
 }
 

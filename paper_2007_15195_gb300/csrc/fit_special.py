@@ -12,9 +12,15 @@ against scipy's double-precision erfcx / erfinv / ndtri:
   Phi^{-1} of the lower tail through erfinv (M. Giles, "Approximating the
   erfinv function", GPU Computing Gems Jade Edition, 2011):
       Phi^{-1}(r) = -sqrt(2) y f(w),  y = 1 - 2r,  w = -ln(4 r (1 - r)),
-      f(w) = erfinv(y) / y, a polynomial in w on [0, 5], in sqrt(w) on
-      [5, 36] and on [36, 130] and [130, 700] (the last two only reached from
-      log-space inputs, r < 5e-17).
+      f(w) = erfinv(y) / y, a polynomial in w on [0, 8] (r > 8.4e-5, the
+      branch almost every lane takes), in sqrt(w) on [8, 36] and on [36, 130]
+      and [130, 700] (the last two reached for r < 5e-17, mostly from
+      log-space inputs).
+
+The quantile pieces are emitted multiplied by sqrt(2), so that
+Phi^{-1}(p) = (p - q) f_s(w) with f_s = sqrt(2) f and q = 1 - p on either
+side of 1/2; the first piece also gets the map from L = log2(r (1 - r)) (so
+w = -ln 2 (L + 2)) folded into its variable, u = a' L + b'.
 
 Each piece is a polynomial in a variable mapped to [-1, 1], fitted in the
 Chebyshev basis by Lawson's iteratively reweighted least squares toward the
@@ -34,6 +40,7 @@ OUT = os.path.join(HERE, "special_f32.cuh")
 LOG2E = 1.4426950408889634
 K_T = 1.0 / (2.0 * np.sqrt(2.0))  # t = 1 / (1 + z K_T)
 Z_MAX = 38.0
+W1_HI = 8.0  # first quantile piece: w in [0, 8], i.e. r > 8.4e-5
 
 
 def lawson_cheb(u, f, deg, iters=60, rel=True):
@@ -94,11 +101,11 @@ def fit_inv(name, lo, hi, var, deg):
     xlo, xhi = (lo, hi) if var == "w" else (np.sqrt(lo), np.sqrt(hi))
     u = (2.0 * x - (xhi + xlo)) / (xhi - xlo)
     c, err = lawson_cheb(u, f, deg, rel=True)
-    mono = to_monomial(c)
+    mono = to_monomial(c) * np.sqrt(2.0)
     got = horner_f32(mono, u)
-    err32 = float(np.max(np.abs(got - f) / np.abs(f)))
+    err32 = float(np.max(np.abs(got - f * np.sqrt(2.0)) / np.abs(f * np.sqrt(2.0))))
     return dict(name=name, a=2.0 / (xhi - xlo), b=-(xhi + xlo) / (xhi - xlo), coef=mono, fit_err=err,
-                f32_err=err32, note="f(w) = erfinv(y)/y on %s in [%g, %g]" % (var, xlo, xhi))
+                f32_err=err32, note="sqrt(2) erfinv(y)/y on %s in [%g, %g]" % (var, xlo, xhi))
 
 
 def emit(pieces):
@@ -117,6 +124,12 @@ def emit(pieces):
         "constexpr float kZmax = %.1ff;" % Z_MAX,
         "",
     ]
+    inv1 = [p for p in pieces if p["name"] == "INV1"][0]
+    ln2 = np.log(2.0)
+    lines.append("// INV1 from L = log2(r (1-r)): u = kINV1LA L + kINV1LB, valid for L > kINV1Lmin")
+    lines.append("constexpr float kINV1LA = %.9ef, kINV1LB = %.9ef, kINV1Lmin = %.9ef;" % (
+        -inv1["a"] * ln2, inv1["b"] - 2.0 * inv1["a"] * ln2, -W1_HI / ln2 - 2.0))
+    lines.append("")
     for p in pieces:
         lines.append("// %s: %s; fit max error %.2e, in float32 %.2e" % (p["name"], p["note"], p["fit_err"],
                                                                          p["f32_err"]))
@@ -133,8 +146,8 @@ def emit(pieces):
 def main():
     pieces = [
         fit_phi(9),
-        fit_inv("INV1", 0.0, 5.0, "w", 8),
-        fit_inv("INV2", 5.0, 36.0, "s", 11),
+        fit_inv("INV1", 0.0, W1_HI, "w", 10),
+        fit_inv("INV2", W1_HI, 36.0, "s", 9),
         fit_inv("INV3", 36.0, 130.0, "s", 8),
         fit_inv("INV4", 130.0, 700.0, "s", 8),
     ]

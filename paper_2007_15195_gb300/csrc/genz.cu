@@ -54,11 +54,15 @@ struct GenzSmem {
     // MIXED divides each row v by L_vv (so the conditional mean is already
     // standardised); FP64 keeps them unscaled and divides by L_vv, as the
     // row-by-row definition does.
-    __align__(16) T Lup[DMAX][DMAX];
+    static constexpr int LS = (DMAX + 3) & ~3;  // row stride: 16-byte aligned rows
+    __align__(16) T Lup[DMAX][LS];
     __align__(16) T Lz[DMAX];
     __align__(16) T up[DMAX];  // MIXED: u_v / L_vv;  FP64: u_v
     uint32_t gl[DMAX];         // FP64: g_t;  MIXED: round(g_t 2^32 / N)
     uint32_t dfix[MIXED ? kMaxS : 1][DMAX];
+    // per warp, the step constants of the shift it is working on:
+    // {L_{t+1,t}/L_{t+1,t+1}, round(g_t 2^32/N), shift_t 2^32, 0}, one 16-byte load per step
+    __align__(16) float4 stepw[MIXED ? kMaxWarps : 1][MIXED ? DMAX : 1];
     double part_num[kMaxUnits], part_den[kMaxUnits];
     double e0, ec0;
     float le2_0;  // log2 e0 when e0 < 2^-64 (mixed path)
@@ -163,7 +167,7 @@ __device__ __forceinline__ void mixed_phases(const GenzSmem<DMAX, true>& sm, con
 }
 
 template <int DMAX, int P>
-__device__ __forceinline__ void genz_points_mixed(const GenzSmem<DMAX, true>& sm, int q, int s,
+__device__ __forceinline__ void genz_points_safe(const GenzSmem<DMAX, true>& sm, int q, int s,
                                                   int64_t k_begin, int64_t k_end, double& acc_num,
                                                   double& acc_den) {
     constexpr int W0 = (DMAX - 2 > 0) ? DMAX - 2 : 1;
@@ -204,6 +208,105 @@ __device__ __forceinline__ void genz_points_mixed(const GenzSmem<DMAX, true>& sm
             }
         }
     }
+}
+
+// ------------------- mixed path, fast form (the common case) -----------------
+// No log-space bookkeeping: a conditional probability below the FP32 range
+// simply zeroes its point's sample.  Such a sample is below 2^-62 in absolute
+// terms, so whenever the term's lattice means are at least 2^-40 the loss is
+// below 2^-22 relative; terms whose means fall under 2^-40 are flagged and
+// re-evaluated by the log-space form above (genz_points_safe).  Sums run in
+// FP32 with Kahan compensation per lane and are folded into FP64 per unit.
+
+struct Kahan32 {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <int DMAX, int P, int W, bool FIRST>
+__device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const float4* sc, int t,
+                                          float (&R)[P][DMAX - 1], float (&e)[P], float (&ec)[P],
+                                          float (&g)[P], const uint32_t (&kk)[P]) {
+    const float* lup = sm.Lup[t];
+    const float4 c = sc[t];
+    const float lz = c.x;
+    const uint32_t G = __float_as_uint(c.y), Dt = __float_as_uint(c.z);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (!FIRST) g[p] = __fmul_rn(g[p], e[p]);  // g = e_1 ... e_t
+        // lattice coordinate in 32-bit fixed point, tent transform w = 1 - |2x - 1|
+        const uint32_t X = kk[p] * G + Dt;
+        const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
+        const float w = __fmul_rn(__uint2float_rn(V), 0x1p-31f);
+        const float y = special::phiinv_pq(__fmul_rn(w, e[p]), fmaf(w, ec[p], __fsub_rn(1.0f, w)));
+        const float z = fmaf(-lz, y, R[p][0]);
+#pragma unroll
+        for (int r = 0; r < W; ++r) R[p][r] = fmaf(-lup[r], y, R[p][r + 1]);
+        special::phi_pair_fast(z, e[p], ec[p]);
+    }
+}
+
+template <int DMAX, int P, int W>
+__device__ __forceinline__ void fast_phases(const GenzSmem<DMAX, true>& sm, const float4* sc, int t,
+                                            int q, float (&R)[P][DMAX - 1], float (&e)[P],
+                                            float (&ec)[P], float (&g)[P], const uint32_t (&kk)[P]) {
+    constexpr int WN = W - 4;
+    const int t_end = (WN > 0) ? max(t, min(q, q - 1 - WN)) : q;
+    int tt = t;
+    if (tt == 0 && t_end > 0) {
+        fast_step<DMAX, P, W, true>(sm, sc, 0, R, e, ec, g, kk);
+        tt = 1;
+    }
+#pragma unroll 2
+    for (; tt < t_end; ++tt) fast_step<DMAX, P, W, false>(sm, sc, tt, R, e, ec, g, kk);
+    if constexpr (WN > 0) fast_phases<DMAX, P, WN>(sm, sc, t_end, q, R, e, ec, g, kk);
+}
+
+template <int DMAX, int P>
+__device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm, int q, int s,
+                                                 int64_t k_begin, int64_t k_end, double& acc_num,
+                                                 double& acc_den) {
+    constexpr int W0 = (DMAX - 2 > 0) ? DMAX - 2 : 1;
+    const int lane = threadIdx.x & 31;
+    float4* sc = const_cast<float4*>(sm.stepw[threadIdx.x >> 5]);
+    __syncwarp();
+    if (lane < q) sc[lane] = make_float4(sm.Lz[lane], __uint_as_float(sm.gl[lane]),
+                                         __uint_as_float(sm.dfix[s][lane]), 0.0f);
+    __syncwarp();
+    const float e0f = (float)sm.e0, ec0f = (float)sm.ec0;
+    Kahan32 kn, kd;
+    for (int64_t kb = k_begin; kb < k_end; kb += 32 * P) {
+        float R[P][DMAX - 1], e[P], ec[P], g[P];
+        uint32_t kk[P];
+        bool valid[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int64_t k = kb + p * 32 + lane;
+            valid[p] = k < k_end;
+            kk[p] = (uint32_t)(valid[p] ? k : k_begin);
+#pragma unroll
+            for (int r = 0; r < DMAX - 1; ++r) R[p][r] = sm.up[1 + r];
+            e[p] = e0f;
+            ec[p] = ec0f;
+            g[p] = 1.0f;
+        }
+        fast_phases<DMAX, P, W0>(sm, sc, 0, q, R, e, ec, g, kk);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (valid[p]) {
+                kd.add(g[p]);
+                kn.add(__fmul_rn(g[p], e[p]));
+            }
+        }
+    }
+    acc_num += kn.value();
+    acc_den += kd.value();
 }
 
 // ------------------------------- FP64 path ---------------------------------
@@ -284,11 +387,36 @@ __device__ __forceinline__ void item_of(const ItemSrc& src, int it, int2& ps, in
     ps = make_int2(src.seg_base[lo].x, src.seg_base[lo].y + (site_item - src.seg_prefix[lo]));
 }
 
-template <int DMAX, int P, bool MIXED>
-__global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ probs, ItemSrc src,
+// MODE: 0 = FP64, 1 = mixed fast form, 2 = mixed log-space form.
+constexpr int kModeFP64 = 0, kModeFast = 1, kModeSafe = 2;
+
+// Register cap per thread: the fast mixed loop keeps DMAX - 1 partial sums per
+// point in registers; capping the rest raises the number of resident warps.
+#ifndef VK_CAP_P1_SMALL
+#define VK_CAP_P1_SMALL 64
+#endif
+#ifndef VK_CAP_P1_LARGE
+#define VK_CAP_P1_LARGE 80
+#endif
+#ifndef VK_CAP_P2_SMALL
+#define VK_CAP_P2_SMALL 96
+#endif
+#ifndef VK_CAP_P2_LARGE
+#define VK_CAP_P2_LARGE 128
+#endif
+__host__ __device__ constexpr int reg_cap(int dmax, int p, int mode) {
+    return mode != kModeFast ? 128
+           : p == 1        ? (dmax <= 16 ? VK_CAP_P1_SMALL : VK_CAP_P1_LARGE)
+                           : (dmax <= 16 ? VK_CAP_P2_SMALL : VK_CAP_P2_LARGE);
+}
+
+template <int DMAX, int P, int MODE>
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(DMAX, P, MODE))
+    genz_kernel(const ProbDev* __restrict__ probs, ItemSrc src,
                                                    int slices, ProbResult* __restrict__ results,
                                                    int* __restrict__ fallback_count,
                                                    int2* __restrict__ fallback_items) {
+    constexpr bool MIXED = MODE != kModeFP64;
     __shared__ GenzSmem<DMAX, MIXED> sm;
     using T = typename GenzSmem<DMAX, MIXED>::T;
     const int lane = threadIdx.x & 31;
@@ -375,8 +503,9 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
 
         if (!sm.bad) {
             // ---- derived tables for the recursion ----
-            for (int x = threadIdx.x; x < DMAX * DMAX; x += blockDim.x) {
-                const int t = x / DMAX, r = x % DMAX, v = t + 2 + r;
+            constexpr int LS = GenzSmem<DMAX, MIXED>::LS;
+            for (int x = threadIdx.x; x < DMAX * LS; x += blockDim.x) {
+                const int t = x / LS, r = x % LS, v = t + 2 + r;
                 T val = (T)0;
                 if (t < q && v < d) {
                     if constexpr (MIXED)
@@ -421,8 +550,10 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
                 const int s = s_lo + un / slices, h = un % slices;
                 const int64_t k0 = (Pd.N * h) / slices, k1 = (Pd.N * (h + 1)) / slices;
                 double an = 0.0, ad = 0.0;
-                if constexpr (MIXED)
-                    genz_points_mixed<DMAX, P>(sm, q, s, k0, k1, an, ad);
+                if constexpr (MODE == kModeFast)
+                    genz_points_fast<DMAX, P>(sm, q, s, k0, k1, an, ad);
+                else if constexpr (MODE == kModeSafe)
+                    genz_points_safe<DMAX, P>(sm, q, s, k0, k1, an, ad);
                 else
                     genz_points_fp64<DMAX>(sm, Pd, q, s, k0, k1, an, ad);
                 an = warp_sum(an);
@@ -455,7 +586,9 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
                 if constexpr (MIXED) {
                     vn *= sm.e0;
                     vd *= sm.e0;
-                    if (!(vn > 0.0) || !(vd > 0.0) || !isfinite(vn) || !isfinite(vd)) sm.flag = 1;
+                    // the fast form is exact to 2^-22 only for means >= 2^-40
+                    if (MODE == kModeFast && !(vn >= 0x1p-40 && vd >= 0x1p-40 && isfinite(vn) && isfinite(vd)))
+                        sm.flag = 1;
                 }
             }
             Pd.num[site * S + s] = vn;
@@ -466,7 +599,7 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
             if (sm.bad) {
                 atomicMin((unsigned long long*)&results[item.x].bad_site, (unsigned long long)site);
                 results[item.x].status = (sm.bad == 1) ? VECCHIA_ERR_NOT_PD : VECCHIA_ERR_ARG;
-            } else if (MIXED && sm.flag && fallback_items) {
+            } else if (MODE == kModeFast && sm.flag && fallback_items) {
                 const int pos = atomicAdd(fallback_count, 1);
                 fallback_items[pos] = item;
             }
@@ -476,59 +609,87 @@ __global__ void __launch_bounds__(512) genz_kernel(const ProbDev* __restrict__ p
 }
 
 // ------------------------------- log-sum ------------------------------------
+// Two passes with a fixed reduction order, so results are bit-identical run to
+// run and alone vs in a batch:
+//   partial: CTA (slice, problem) takes sites slice*256 .. +255, forms each
+//     term T_i = log mean_s num - log mean_s den (Sec. 3.1: every term on the
+//     log scale) and the delta-method pieces num_is/numbar_i - den_is/denbar_i,
+//     and writes their slice sums;
+//   final: one warp per problem adds the slices in order and forms
+//     log P = sum_i T_i and SE = sqrt(sum_s l_s^2 / (S (S-1))).
 
-constexpr int kSumThreads = 256;
+constexpr int kSliceSites = 256;
 
-__device__ double block_sum(double v, double* red) {
-    const int tid = threadIdx.x;
-    red[tid] = v;
-    __syncthreads();
-    for (int o = kSumThreads / 2; o > 0; o >>= 1) {
-        if (tid < o) red[tid] += red[tid + o];
-        __syncthreads();
-    }
-    const double r = red[0];
-    __syncthreads();
-    return r;
+__device__ __forceinline__ double warp_sum_xor(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-__global__ void __launch_bounds__(kSumThreads) logsum_kernel(const ProbDev* __restrict__ probs,
-                                                             ProbResult* __restrict__ results,
-                                                             double* const* __restrict__ terms,
-                                                             double* __restrict__ means,
-                                                             const int64_t* __restrict__ means_off) {
-    __shared__ double red[kSumThreads];
-    const int pi = blockIdx.x;
+__global__ void __launch_bounds__(kSliceSites) logsum_partial_kernel(
+    const ProbDev* __restrict__ probs, double* const* __restrict__ terms, double* __restrict__ scratch,
+    const int64_t* __restrict__ scratch_off) {
+    __shared__ double red[kMaxS + 1][kSliceSites / 32];
+    const int pi = blockIdx.y, slice = blockIdx.x;
     const ProbDev& Pd = probs[pi];
     const int64_t D = Pd.D;
     const int S = Pd.S;
-    double* nb = means + means_off[pi];
-    double* db = nb + D;
-    double* tout = terms ? terms[pi] : nullptr;
-    double tsum = 0.0;
-    for (int64_t i = threadIdx.x; i < D; i += kSumThreads) {
+    if ((int64_t)slice * kSliceSites >= D) return;  // CTA-uniform
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)slice * kSliceSites + tid;
+    const bool valid = i < D;
+    double T = 0.0, a = 1.0, b = 1.0;
+    if (valid) {
         double sn = 0.0, sd = 0.0;
         for (int s = 0; s < S; ++s) {
             sn += Pd.num[i * S + s];
             sd += Pd.den[i * S + s];
         }
-        const double a = sn / (double)S, b = sd / (double)S;
-        nb[i] = a;
-        db[i] = b;
-        const double T = log(a) - log(b);  // each term on the log scale (Sec. 3.1)
-        if (tout) tout[i] = T;
-        tsum += T;
+        a = sn / (double)S;
+        b = sd / (double)S;
+        T = log(a) - log(b);
+        if (terms && terms[pi]) terms[pi][i] = T;
     }
-    const double log_p = block_sum(tsum, red);
-    double ss = 0.0;
+    double v = warp_sum_xor(T);
+    if (lane == 0) red[0][warp] = v;
     for (int s = 0; s < S; ++s) {
-        double l = 0.0;
-        for (int64_t i = threadIdx.x; i < D; i += kSumThreads)
-            l += Pd.num[i * S + s] / nb[i] - Pd.den[i * S + s] / db[i];
-        const double ls = block_sum(l, red);
-        ss += ls * ls;
+        const double c = valid ? Pd.num[i * S + s] / a - Pd.den[i * S + s] / b : 0.0;
+        v = warp_sum_xor(c);
+        if (lane == 0) red[1 + s][warp] = v;
     }
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    double* out = scratch + scratch_off[pi] + (int64_t)slice * (S + 1);
+    for (int c = tid; c <= S; c += blockDim.x) {
+        double acc = 0.0;
+        for (int w = 0; w < kSliceSites / 32; ++w) acc += red[c][w];
+        out[c] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(32) logsum_final_kernel(const ProbDev* __restrict__ probs,
+                                                          ProbResult* __restrict__ results,
+                                                          const double* __restrict__ scratch,
+                                                          const int64_t* __restrict__ scratch_off) {
+    const int pi = blockIdx.x, lane = threadIdx.x;
+    const ProbDev& Pd = probs[pi];
+    const int64_t D = Pd.D;
+    const int S = Pd.S;
+    if (D <= 0 || S < 2) return;
+    const int slices = (int)((D + kSliceSites - 1) / kSliceSites);
+    const double* part = scratch + scratch_off[pi];
+    double col[3] = {0.0, 0.0, 0.0};  // columns lane, lane + 32, lane + 64 (S + 1 <= 65)
+    for (int k = 0; k < 3; ++k) {
+        const int c = lane + 32 * k;
+        if (c <= S)
+            for (int sl = 0; sl < slices; ++sl) col[k] += part[(int64_t)sl * (S + 1) + c];
+    }
+    double log_p = __shfl_sync(0xffffffffu, col[0], 0);
+    double ss = 0.0;
+    for (int c = 1; c <= S; ++c) {
+        const double l = __shfl_sync(0xffffffffu, col[c >> 5], c & 31);
+        ss += l * l;
+    }
+    if (lane == 0) {
         ProbResult& R = results[pi];
         R.log_p = log_p;
         R.std_err = sqrt(ss / ((double)S * (double)(S - 1)));
@@ -615,10 +776,10 @@ cudaError_t launch_eval_special(int which, const float* x, int64_t n, float* out
 
 namespace {
 
-template <int DMAX, int P, bool MIXED>
+template <int DMAX, int P, int MODE>
 cudaError_t launch_one(const GenzTile& tile, const ProbDev* probs, const ItemSrc& src,
                        ProbResult* results, int* fb_count, int2* fb_items, cudaStream_t st) {
-    auto kern = genz_kernel<DMAX, P, MIXED>;
+    auto kern = genz_kernel<DMAX, P, MODE>;
     static int per_sm[kMaxWarps + 1] = {0};
     const int warps = tile.warps < 1 ? 1 : (tile.warps > kMaxWarps ? kMaxWarps : tile.warps);
     int dev = 0;
@@ -650,19 +811,21 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
     const int per_group = (max_S + t.groups - 1) / t.groups;
     while (t.slices > 1 && per_group * t.slices > kMaxUnits) --t.slices;
     ItemSrc src{nullptr, nullptr, seg_prefix, seg_base, n_segs, n_sites * t.groups, t.groups};
-#define VK_CASE(DM)                                                                              \
-    case DM / 8 - 1:                                                                             \
-        if (!mixed) return launch_one<DM, 1, false>(t, probs, src, results, nullptr, nullptr, st); \
-        if (t.points >= 4)                                                                       \
-            return launch_one<DM, 4, true>(t, probs, src, results, fallback_count, fallback_items, st); \
-        if (t.points == 2)                                                                       \
-            return launch_one<DM, 2, true>(t, probs, src, results, fallback_count, fallback_items, st); \
-        return launch_one<DM, 1, true>(t, probs, src, results, fallback_count, fallback_items, st);
+#define VK_CASE(IDX, DM)                                                                         \
+    case IDX:                                                                                    \
+        if (!mixed) return launch_one<DM, 1, kModeFP64>(t, probs, src, results, nullptr, nullptr, st); \
+        if (t.points >= 2)                                                                       \
+            return launch_one<DM, 2, kModeFast>(t, probs, src, results, fallback_count, fallback_items, st); \
+        return launch_one<DM, 1, kModeFast>(t, probs, src, results, fallback_count, fallback_items, st);
+    static_assert(kNumBuckets == 7, "bucket table");
     switch (bucket) {
-        VK_CASE(8)
-        VK_CASE(16)
-        VK_CASE(24)
-        VK_CASE(32)
+        VK_CASE(0, 9)
+        VK_CASE(1, 13)
+        VK_CASE(2, 17)
+        VK_CASE(3, 21)
+        VK_CASE(4, 25)
+        VK_CASE(5, 29)
+        VK_CASE(6, 32)
         default:
             return cudaErrorInvalidValue;
     }
@@ -675,14 +838,16 @@ cudaError_t launch_genz_fallback(const ProbDev* probs, const int* fallback_count
     if (capacity <= 0) return cudaSuccess;
     GenzTile t{4, 1, 1, 1};
     ItemSrc src{fallback_items, fallback_count, nullptr, nullptr, 0, capacity, 1};
-    return launch_one<32, 1, false>(t, probs, src, results, nullptr, nullptr, st);
+    return launch_one<32, 1, kModeSafe>(t, probs, src, results, nullptr, nullptr, st);
 }
 
-cudaError_t launch_logsum(const ProbDev* probs, int n_probs, ProbResult* results,
-                          double* const* terms, double* scratch_means, const int64_t* means_off,
+cudaError_t launch_logsum(const ProbDev* probs, int n_probs, int max_slices, ProbResult* results,
+                          double* const* terms, double* scratch, const int64_t* scratch_off,
                           cudaStream_t st) {
-    if (n_probs <= 0) return cudaSuccess;
-    logsum_kernel<<<n_probs, kSumThreads, 0, st>>>(probs, results, terms, scratch_means, means_off);
+    if (n_probs <= 0 || max_slices <= 0) return cudaSuccess;
+    logsum_partial_kernel<<<dim3(max_slices, n_probs), kSliceSites, 0, st>>>(probs, terms, scratch,
+                                                                          scratch_off);
+    logsum_final_kernel<<<n_probs, 32, 0, st>>>(probs, results, scratch, scratch_off);
     return cudaGetLastError();
 }
 

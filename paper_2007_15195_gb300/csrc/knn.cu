@@ -9,10 +9,11 @@
 //     distance ties go to the smaller index;
 //   - bucket the sites into a (G+1) x (G+1) grid of square cells of side
 //     2^(30 - log2 G) by a counting sort;
-//   - per site, visit rings of cells of growing Chebyshev radius r around the
-//     site's cell, keeping the best q keys among sites j < i; after ring r every
-//     unvisited site is at least r*cell + 1 away in one coordinate, so the
-//     search stops once the q-th best squared distance is below (r*cell + 1)^2;
+//   - one warp per site visits rings of cells of growing Chebyshev radius r
+//     around the site's cell, keeping the best q keys among sites j < i in a
+//     warp-wide sorted list; after ring r every unvisited site is at least
+//     r*cell + 1 away in one coordinate, so the search stops once the q-th
+//     best squared distance is below (r*cell + 1)^2;
 //   - sites with a small index are searched by brute force over j < i.
 #include <climits>
 
@@ -22,7 +23,7 @@ namespace vk {
 namespace {
 
 constexpr int kMaxQ = 32;
-constexpr int kBruteLimit = 2048;
+constexpr int kBruteLimit = 512;
 
 struct Grid {
     double xmin, ymin, c;
@@ -132,56 +133,134 @@ __global__ void scatter_kernel(const int2* __restrict__ qxy, int64_t D, const Gr
     cell_pts[pos] = make_int4(q.x, q.y, (int)i, 0);
 }
 
-struct TopQ {
-    long long kd[kMaxQ];
-    int kj[kMaxQ];
-    int n, q;
+// ---- warp-wide top-q list -------------------------------------------------
+// A key is (squared quantised distance, index), compared lexicographically.
+// Lane r of a warp holds the r-th smallest key seen so far (r < 32 >= q).
+// Candidates arrive in chunks of up to 32 (one per lane): a chunk is sorted
+// across lanes by a bitonic network, reversed and merged with the list by an
+// element-wise minimum (the 32 smallest of the union form a bitonic sequence),
+// which a bitonic clean-up sorts again.
 
-    __device__ __forceinline__ void consider(long long d2, int j) {
-        if (n == q) {
-            const long long wd = kd[q - 1];
-            if (d2 > wd || (d2 == wd && j > kj[q - 1])) return;
-        }
-        int pos = (n < q) ? n : q - 1;
-        if (n < q) ++n;
-        while (pos > 0 && (kd[pos - 1] > d2 || (kd[pos - 1] == d2 && kj[pos - 1] > j))) {
-            kd[pos] = kd[pos - 1];
-            kj[pos] = kj[pos - 1];
-            --pos;
-        }
-        kd[pos] = d2;
-        kj[pos] = j;
-    }
+struct Key {
+    unsigned long long d2;
+    int j;
 };
 
-__device__ __forceinline__ long long qdist2(int ax, int ay, int bx, int by) {
-    const long long dx = (long long)ax - bx, dy = (long long)ay - by;
-    return dx * dx + dy * dy;
+constexpr unsigned long long kInfD2 = ~0ULL;
+
+__device__ __forceinline__ bool key_less(const Key& a, const Key& b) {
+    return a.d2 < b.d2 || (a.d2 == b.d2 && a.j < b.j);
 }
 
-__global__ void __launch_bounds__(128) search_kernel(const int2* __restrict__ qxy, int64_t D, int m,
-                                                     const Grid* __restrict__ grid,
-                                                     const int* __restrict__ offsets,
-                                                     const int4* __restrict__ cell_pts,
-                                                     int32_t* __restrict__ nbr) {
-    const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i64 >= D) return;
+__device__ __forceinline__ Key shfl_key(const Key& k, int src) {
+    Key o;
+    o.d2 = __shfl_sync(0xffffffffu, k.d2, src);
+    o.j = __shfl_sync(0xffffffffu, k.j, src);
+    return o;
+}
+
+__device__ __forceinline__ Key shfl_xor_key(const Key& k, int m) {
+    Key o;
+    o.d2 = __shfl_xor_sync(0xffffffffu, k.d2, m);
+    o.j = __shfl_xor_sync(0xffffffffu, k.j, m);
+    return o;
+}
+
+// one compare-exchange stage: partner lane ^ jm; blocks of size kb ascending
+__device__ __forceinline__ void cx(Key& k, int lane, int kb, int jm) {
+    const Key o = shfl_xor_key(k, jm);
+    const bool up = (lane & kb) == 0;
+    const bool lower = (lane & jm) == 0;
+    const bool keep_min = (lower == up);
+    const bool mine_less = key_less(k, o);
+    if (keep_min != mine_less) k = o;
+}
+
+__device__ __forceinline__ void bitonic_sort32(Key& k, int lane) {
+#pragma unroll
+    for (int kb = 2; kb <= 32; kb <<= 1)
+#pragma unroll
+        for (int jm = kb >> 1; jm > 0; jm >>= 1) cx(k, lane, kb, jm);
+}
+
+// list (ascending) <- 32 smallest of list and chunk
+__device__ __forceinline__ void merge_chunk(Key& list, Key c, int lane) {
+    bitonic_sort32(c, lane);
+    const Key rev = shfl_key(c, 31 - lane);
+    if (key_less(rev, list)) list = rev;
+#pragma unroll
+    for (int jm = 16; jm > 0; jm >>= 1) cx(list, lane, 64, jm);  // 64: one ascending block
+}
+
+__device__ __forceinline__ unsigned long long qdist2(int ax, int ay, int bx, int by) {
+    const long long dx = (long long)ax - bx, dy = (long long)ay - by;
+    return (unsigned long long)(dx * dx + dy * dy);
+}
+
+constexpr int kSearchWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSearchWarps) search_kernel(
+    const int2* __restrict__ qxy, int64_t D, int m, const Grid* __restrict__ grid,
+    const int* __restrict__ offsets, const int4* __restrict__ cell_pts, int32_t* __restrict__ nbr) {
+    __shared__ Key stage[kSearchWarps][64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t i64 = (int64_t)blockIdx.x * kSearchWarps + wid;
+    if (i64 >= D) return;  // warp-uniform
     const int i = (int)i64;
     const int q = (i < m) ? i : m;
     int32_t* out = nbr + i64 * m;
     if (q == i) {  // every previous site is a neighbour
-        for (int r = 0; r < m; ++r) out[r] = (r < i) ? r : -1;
+        for (int r = lane; r < m; r += 32) out[r] = (r < i) ? r : -1;
         return;
     }
-    TopQ top;
-    top.n = 0;
-    top.q = q;
+    Key list;
+    list.d2 = kInfD2;
+    list.j = INT_MAX;
     const int2 me = qxy[i];
-    if (i < kBruteLimit) {
-        for (int j = 0; j < i; ++j) {
-            const int2 o = qxy[j];
-            top.consider(qdist2(me.x, me.y, o.x, o.y), j);
+    Key* st = stage[wid];
+    int n = 0;  // staged candidates (warp-uniform)
+    auto worst = [&]() { return shfl_key(list, q - 1); };
+    // stage the lanes' candidates that beat the current q-th best; merge full chunks
+    auto offer = [&](bool valid, Key k) {
+        const Key w = worst();
+        valid = valid && key_less(k, w);
+        const unsigned mask = __ballot_sync(0xffffffffu, valid);
+        if (valid) st[n + __popc(mask & ((1u << lane) - 1u))] = k;
+        n += __popc(mask);
+        __syncwarp();
+        if (n >= 32) {
+            merge_chunk(list, st[lane], lane);
+            __syncwarp();
+            if (lane < n - 32) st[lane] = st[32 + lane];
+            n -= 32;
+            __syncwarp();
         }
+    };
+    auto flush = [&]() {
+        if (n > 0) {
+            Key c;
+            c.d2 = kInfD2;
+            c.j = INT_MAX;
+            if (lane < n) c = st[lane];
+            merge_chunk(list, c, lane);
+            n = 0;
+            __syncwarp();
+        }
+    };
+    if (i < kBruteLimit) {
+        for (int base = 0; base < i; base += 32) {
+            const int j = base + lane;
+            Key k;
+            k.d2 = kInfD2;
+            k.j = INT_MAX;
+            if (j < i) {
+                const int2 o = qxy[j];
+                k.d2 = qdist2(me.x, me.y, o.x, o.y);
+                k.j = j;
+            }
+            offer(j < i, k);
+        }
+        flush();
     } else {
         const Grid g = *grid;
         const int G = g.G, W = G + 1;
@@ -191,35 +270,42 @@ __global__ void __launch_bounds__(128) search_kernel(const int2* __restrict__ qx
             for (int cy = cy0 - r; cy <= cy0 + r; ++cy) {
                 if (cy < 0 || cy > G) continue;
                 const bool edge_row = (cy == cy0 - r) || (cy == cy0 + r);
-                const int step = edge_row ? 1 : 2 * r;
-                for (int cx = cx0 - r; cx <= cx0 + r; cx += (step > 0 ? step : 1)) {
-                    if (cx < 0 || cx > G) continue;
-                    const int cell = cy * W + cx;
+                const int step = (edge_row || r == 0) ? 1 : 2 * r;
+                for (int cxx = cx0 - r; cxx <= cx0 + r; cxx += step) {
+                    if (cxx < 0 || cxx > G) continue;
+                    const int cell = cy * W + cxx;
                     const int b = offsets[cell], e = offsets[cell + 1];
-                    for (int p = b; p < e; ++p) {
-                        const int4 o = cell_pts[p];
-                        if (o.z < i) top.consider(qdist2(me.x, me.y, o.x, o.y), o.z);
+                    for (int base = b; base < e; base += 32) {
+                        const int p = base + lane;
+                        Key k;
+                        k.d2 = kInfD2;
+                        k.j = INT_MAX;
+                        bool valid = false;
+                        if (p < e) {
+                            const int4 o = cell_pts[p];
+                            valid = o.z < i;
+                            k.d2 = qdist2(me.x, me.y, o.x, o.y);
+                            k.j = o.z;
+                        }
+                        offer(valid, k);
                     }
                 }
             }
-            if (top.n == q) {
+            flush();
+            const Key w = worst();
+            if (w.d2 != kInfD2) {
                 const long long bound = (long long)r * cs + 1;
-                if (top.kd[q - 1] < bound * bound) break;
+                if (w.d2 < (unsigned long long)(bound * bound)) break;
             }
             if (cx0 - r <= 0 && cy0 - r <= 0 && cx0 + r >= G && cy0 + r >= G) break;
         }
     }
-    // list ascending by index (the block order of Sec. 2.2)
-    for (int a = 1; a < top.n; ++a) {
-        const int v = top.kj[a];
-        int b = a - 1;
-        while (b >= 0 && top.kj[b] > v) {
-            top.kj[b + 1] = top.kj[b];
-            --b;
-        }
-        top.kj[b + 1] = v;
-    }
-    for (int r = 0; r < m; ++r) out[r] = (r < top.n) ? top.kj[r] : -1;
+    // lanes < q hold the q nearest; list them ascending by index (Sec. 2.2 block order)
+    Key byj;
+    byj.d2 = 0;
+    byj.j = (lane < q) ? list.j : INT_MAX;
+    bitonic_sort32(byj, lane);
+    if (lane < m) out[lane] = (lane < q) ? byj.j : -1;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -280,7 +366,8 @@ cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void
     quantize_kernel<<<blocks, 256, 0, st>>>(sites, D, grid, qxy, counts);
     scan_kernel<<<1, 1024, 0, st>>>(counts, (int)cells, offsets, cursor);
     scatter_kernel<<<blocks, 256, 0, st>>>(qxy, D, grid, cursor, cell_pts);
-    search_kernel<<<(int)((D + 127) / 128), 128, 0, st>>>(qxy, D, m, grid, offsets, cell_pts, nbr);
+    search_kernel<<<(int)((D + kSearchWarps - 1) / kSearchWarps), 32 * kSearchWarps, 0, st>>>(
+        qxy, D, m, grid, offsets, cell_pts, nbr);
     return cudaGetLastError();
 }
 

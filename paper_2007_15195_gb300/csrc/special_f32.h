@@ -4,10 +4,14 @@
 // Phi of the lower tail (Numerical Recipes "erfcc" form, own coefficients):
 //     Phi(-z) = t 2^(a),  t = 1/(1 + z/(2 sqrt 2)),  a = -z^2 log2(e)/2 + P(t),  z >= 0.
 // log2 Phi(-z) = log2 t + a is available without underflow.
-// Phi^{-1} of the lower tail (M. Giles' erfinv form, own coefficients):
-//     Phi^{-1}(r) = -sqrt(2) y f(w),  y = 1 - 2r,  w = -ln(4 r (1 - r)).
-// From a log-probability (r < 2^-64): w = -(ln 4 + ln r), y = 1.
-// Coefficients: special_f32.cuh (generated by fit_special.py).
+// Phi^{-1} (M. Giles' erfinv form, own coefficients), from p and q = 1 - p:
+//     Phi^{-1}(p) = (p - q) f_s(w),  w = -ln(4 p q),  f_s = sqrt(2) erfinv(y)/y,
+// the sign coming from p - q; the central piece is evaluated straight from
+// L = log2(p q).  From a log-probability (r < 2^-64): w = -(ln 4 + ln r).
+// Coefficients: special_f32.cuh (generated by fit_special.py).  Products and
+// sums are written with explicit rounding (__fmul_rn, __fsub_rn, fmaf) so the
+// compiler cannot contract them differently from one instantiation to the
+// next: every kernel variant computes bit-identical values.
 #pragma once
 
 #include "special_f32.cuh"
@@ -19,7 +23,7 @@ constexpr float kLn2 = 0.693147180559945309f;
 constexpr float kLn4 = 1.38629436111989062f;
 constexpr float kSqrt2 = 1.41421356237309505f;
 constexpr float kTinyZ = -9.0f;   // Phi(-9) ~ 2^-62.5: below, carry log2 Phi instead
-constexpr float kFloor = 1.17549435e-38f;  // smallest normal float: clamp of r
+constexpr float kFloor = 2.35098870e-38f;  // 2^-125: r q stays a normal float
 
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -57,41 +61,51 @@ __device__ __forceinline__ float horner(const float (&c)[N], float u) {
 __device__ __forceinline__ void phi_pair(float z, float& e, float& ec, bool& tiny, float& le2) {
     const float az = fminf(fabsf(z), kZmax);
     const float t = rcp(fmaf(az, kKt, 1.0f));
-    const float a = fmaf(az * (-0.5f * kLog2e), az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
-    const float tail = t * ex2(a);  // Phi(-|z|)
+    const float a = fmaf(__fmul_rn(az, -0.5f * kLog2e), az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float tail = __fmul_rn(t, ex2(a));  // Phi(-|z|)
     const bool neg = z < 0.0f;
-    e = neg ? tail : 1.0f - tail;
-    ec = neg ? 1.0f - tail : tail;
+    e = neg ? tail : __fsub_rn(1.0f, tail);
+    ec = neg ? __fsub_rn(1.0f, tail) : tail;
     tiny = z < kTinyZ;
     if (tiny) le2 = lg2(t) + a;
 }
 
-// f(w) = erfinv(y)/y for w >= 5 (sqrt(w) pieces).
+// Phi(z) and 1 - Phi(z) without the log-space output (e flushes to 0 below 2^-126).
+__device__ __forceinline__ void phi_pair_fast(float z, float& e, float& ec) {
+    const float az = fminf(fabsf(z), kZmax);
+    const float t = rcp(fmaf(az, kKt, 1.0f));
+    const float a = fmaf(__fmul_rn(az, -0.5f * kLog2e), az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float tail = __fmul_rn(t, ex2(a));
+    const bool neg = z < 0.0f;
+    e = neg ? tail : __fsub_rn(1.0f, tail);
+    ec = neg ? __fsub_rn(1.0f, tail) : tail;
+}
+
+// f_s(w) = sqrt(2) erfinv(y)/y for w >= 8 (sqrt(w) pieces).
 __device__ __forceinline__ float finv_tail(float w) {
     const float s = sqrt_approx(w);
-    if (s < 6.0f) return horner(kINV2C, fmaf(s, kINV2A, kINV2B));
+    if (s < 6.0f) return horner(kINV2C, fmaf(s, kINV2A, kINV2B));  // w in [8, 36)
     if (s < 11.4017543f) return horner(kINV3C, fmaf(s, kINV3A, kINV3B));
     return horner(kINV4C, fmaf(fminf(s, 26.4575131f), kINV4A, kINV4B));
 }
 
-// Phi^{-1}(p) given p and q = 1 - p (both >= 0): from the smaller tail.
+// Phi^{-1}(p) given p and q = 1 - p (both >= 0).
 __device__ __forceinline__ float phiinv_pq(float p, float q) {
     const float r = fmaxf(fminf(p, q), kFloor);
     const float o = fmaxf(p, q);
-    const float w = -kLn2 * lg2(4.0f * r * o);
+    const float L = lg2(__fmul_rn(r, o));  // w = -ln 2 (L + 2)
     float f;
-    if (w < 5.0f)
-        f = horner(kINV1C, fmaf(w, kINV1A, kINV1B));
+    if (L > kINV1Lmin)
+        f = horner(kINV1C, fmaf(L, kINV1LA, kINV1LB));
     else
-        f = finv_tail(w);
-    const float x = kSqrt2 * (o - r) * f;  // -Phi^{-1}(r) >= 0
-    return (p <= q) ? -x : x;
+        f = finv_tail(__fmul_rn(-kLn2, __fadd_rn(L, 2.0f)));
+    return __fmul_rn(__fsub_rn(p, q), f);
 }
 
 // Phi^{-1}(r) for r = 2^lr2 < 2^-64 (log2 input).
 __device__ __forceinline__ float phiinv_log2(float lr2) {
-    const float w = -(kLn4 + kLn2 * fmaxf(lr2, -1009.0f));
-    return -kSqrt2 * finv_tail(w);
+    const float w = -fmaf(kLn2, fmaxf(lr2, -1009.0f), kLn4);
+    return -finv_tail(w);
 }
 
 }  // namespace special

@@ -14,13 +14,16 @@
 namespace vk {
 
 // Bucketed block sizes: a site with q neighbours has d = q + 1 <= 32
-// variables; its Genz kernel is instantiated for the smallest DMAX >= d.
-constexpr int kDmaxBuckets[4] = {8, 16, 24, 32};
+// variables; its problem's Genz kernel is instantiated for the smallest
+// DMAX >= m + 1.  The buckets put m = 8, 12, 16, 20, 24, 28 at the top of
+// theirs, so a lane keeps exactly m partial sums in registers there.
+constexpr int kNumBuckets = 7;
+constexpr int kDmaxBuckets[kNumBuckets] = {9, 13, 17, 21, 25, 29, 32};
 constexpr int kMaxS = VECCHIA_MAX_S;
 constexpr int kMaxDim = 32;  // lattice coordinates per problem (q <= 31)
 
 inline int bucket_of(int d) {
-    for (int b = 0; b < 4; ++b)
+    for (int b = 0; b < kNumBuckets; ++b)
         if (d <= kDmaxBuckets[b]) return b;
     return -1;
 }
@@ -75,9 +78,12 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
 cudaError_t launch_genz_fallback(const ProbDev* probs, const int* fallback_count,
                                  const int2* fallback_items, int capacity, ProbResult* results,
                                  cudaStream_t st);
-// Per-problem deterministic log-sum and standard error; writes results and terms.
-cudaError_t launch_logsum(const ProbDev* probs, int n_probs, ProbResult* results,
-                          double* const* terms, double* scratch_means, const int64_t* means_off,
+// Per-problem deterministic log-sum and standard error; writes results and
+// terms.  scratch_off[p] points at logsum_scratch(D_p, S_p) doubles.
+inline int64_t logsum_slices(int64_t D) { return (D + 255) / 256; }
+inline int64_t logsum_scratch(int64_t D, int S) { return logsum_slices(D) * (S + 1); }
+cudaError_t launch_logsum(const ProbDev* probs, int n_probs, int max_slices, ProbResult* results,
+                          double* const* terms, double* scratch, const int64_t* scratch_off,
                           cudaStream_t st);
 // Shift tables on the device: delta (S x dim FP64) and dfix (S x dim uint32).
 cudaError_t launch_shifts(const uint64_t* seeds, const int32_t* S, const int64_t* out_off,

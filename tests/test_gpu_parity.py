@@ -285,13 +285,13 @@ def test_tiles_change_only_sum_order(ctx):
     for prec in (B.FP64, B.MIXED):
         B.vecchia_reset_tiles(ctx)
         ref = B.vecchia_log_cdf(ctx, s, nbr, 20, prob.cov, u, prob.N, prob.S, 1, prec)
-        for warps, points, slices, groups in [(1, 1, 1, 1), (8, 4, 1, 8), (4, 2, 4, 2), (16, 1, 2, 3)]:
+        for warps, points, slices, groups in [(1, 1, 1, 1), (8, 2, 1, 8), (4, 2, 4, 2), (16, 1, 2, 3)]:
             B.vecchia_set_tile(ctx, prec, -1, warps, points, slices, groups)
             lp, se = B.vecchia_log_cdf(ctx, s, nbr, 20, prob.cov, u, prob.N, prob.S, 1, prec)
-            if slices == 1 and (prec == B.FP64 or points == 1):
+            if slices == 1:  # same points per lane in the same order: bit-identical
                 assert (lp, se) == ref
-            else:
-                assert lp == pytest.approx(ref[0], rel=1e-12)
+            else:  # other point subsets per lane: FP64 sums reorder at 1e-16, FP32 Kahan at ~1e-9
+                assert lp == pytest.approx(ref[0], rel=1e-12 if prec == B.FP64 else 1e-8)
         B.vecchia_reset_tiles(ctx)
 
 

@@ -35,9 +35,10 @@ def test_phi_relative_error_of_the_smaller_tail(ctx):
     small = np.where(xf < 0, e, ec)
     small_ref = np.where(xf < 0, ref, refc)
     # Phi(-|x|) = t 2^a with a ~ -x^2 log2(e)/2: the FP32 rounding of a moves
-    # the result by ~|a| 2^-24 ln 2 relative, on top of the 2e-7 of the fit.
+    # the result by ~|a| 2^-24 ln 2 relative, on top of ~5e-7 from the fit and the
+    # approximate reciprocal and exponential.
     a = 0.5 * xf * xf * np.log2(np.e)
-    bound = 3e-7 + 1.2e-7 * np.maximum(a, 1.0)
+    bound = 8e-7 + 1.2e-7 * np.maximum(a, 1.0)
     assert np.all(np.abs(small - small_ref) / small_ref < bound)
     assert np.max(np.abs(e - ref)) < 2e-7
 
