@@ -181,6 +181,33 @@ int vecchia_genz_time_ms(const vecchia_ctx* ctx, double* ms);
  * in the precision the mixed path evaluates them. */
 int vecchia_eval_special(vecchia_ctx* ctx, int which, const float* x, int64_t n, float* out);
 
+/* Size of the fixed device array that vecchia_log_cdf_noalloc uses as scratch. */
+#define VECCHIA_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* vecchia_log_cdf for callers that cannot allocate memory (the paper has no
+ * counterpart; this is a deployment variant of the same kernels).  Code that
+ * runs while a CUDA graph is being captured, programs whose allocator owns the
+ * whole device and forbids foreign cudaMalloc calls, and hosts that keep no
+ * vecchia_ctx cannot use the context's scratch arena.  This entry point keeps
+ * all of its scratch in one file-scope device array of
+ * VECCHIA_NOALLOC_SCRATCH_BYTES (32 MiB, held by every GPU that loads the
+ * library until the process exits) and calls no allocating routine: no
+ * cudaMalloc, cudaFree or cudaMallocHost, and no context is needed.
+ *   device, cuda_stream: where to run (stream NULL = legacy default stream).
+ *   sites_ordered (D x 2), nbr (D x m), u (D): device memory, as for
+ *   vecchia_log_cdf; log_p, std_err: host scalars.
+ * A problem whose scratch (about 16 D S + 16 D bytes, plus 8 D per shift group
+ * on the mixed path) exceeds the array returns VECCHIA_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address (once per
+ * device, under a lock); make that first call before any stream capture.
+ * Every call shares the array and clears what must start at zero; calls
+ * whose work overlaps on the GPU (other streams or host threads on the same
+ * device) race on it and must be serialised by the caller.  Results equal
+ * vecchia_log_cdf's with the built-in tile. */
+int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const double* sites_ordered, int64_t D,
+                            const int32_t* nbr, int m, vecchia_cov cov, const double* u, int64_t N,
+                            int S, uint64_t seed, int precision, double* log_p, double* std_err);
+
 /* Ordered index of the site whose block failed in the last call (or -1). */
 int64_t vecchia_last_error_site(const vecchia_ctx* ctx);
 

@@ -88,6 +88,10 @@ def lib():
         L.vecchia_reset_tiles.argtypes = [_vp]
         L.vecchia_set_timing.argtypes = [_vp, C.c_int]
         L.vecchia_eval_special.argtypes = [_vp, C.c_int, _vp, C.c_int64, _vp]
+        L.vecchia_log_cdf_noalloc.argtypes = [C.c_int, _vp, _vp, C.c_int64, _vp, C.c_int, vecchia_cov,
+                                              _vp, C.c_int64, C.c_int, C.c_uint64, C.c_int,
+                                              C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.vecchia_genz_time_ms.argtypes = [_vp, C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -232,6 +236,20 @@ def vecchia_log_cdf(ctx, sites_ordered, nbr, m, cov, u, N, S, seed=0, precision=
     _check(lib().vecchia_log_cdf(ctx.handle, _ptr(s), s.shape[0], _ptr(nb), int(m), make_cov(cov),
                                  _ptr(uu), int(N), int(S), C.c_uint64(int(seed)), int(precision),
                                  C.byref(lp), C.byref(se)), "vecchia_log_cdf", ctx)
+    return lp.value, se.value
+
+
+def vecchia_log_cdf_noalloc(device, stream, sites_ordered, nbr, m, cov, u, N, S, seed=0,
+                            precision=MIXED):
+    """The log-CDF with no allocation (scratch in the library's fixed device
+    array); device arrays in, (log_p, std_err) out.  No context is used."""
+    s, uu = _f64(sites_ordered), _f64(u)
+    nb = _i32(nbr) if m > 0 else None
+    lp, se = C.c_double(), C.c_double()
+    _check(lib().vecchia_log_cdf_noalloc(int(device), _vp(stream or 0), _ptr(s), s.shape[0], _ptr(nb),
+                                         int(m), make_cov(cov), _ptr(uu), int(N), int(S),
+                                         C.c_uint64(int(seed)), int(precision), C.byref(lp), C.byref(se)),
+           "vecchia_log_cdf_noalloc")
     return lp.value, se.value
 
 
