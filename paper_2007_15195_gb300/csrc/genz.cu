@@ -252,19 +252,15 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
     }
 }
 
+// Steps t0 <= t < q (t0 >= 1) in phases of update width W, W - 4, ...: a step
+// needs width q - t - 1, so the phase of width W ends where W - 4 suffices.
 template <int DMAX, int P, int W>
 __device__ __forceinline__ void fast_phases(const GenzSmem<DMAX, true>& sm, const float4* sc, int t,
                                             int q, float (&R)[P][DMAX - 1], float (&e)[P],
                                             float (&ec)[P], float (&g)[P], const uint32_t (&kk)[P]) {
     constexpr int WN = W - 4;
     const int t_end = (WN > 0) ? max(t, min(q, q - 1 - WN)) : q;
-    int tt = t;
-    if (tt == 0 && t_end > 0) {
-        fast_step<DMAX, P, W, true>(sm, sc, 0, R, e, ec, g, kk);
-        tt = 1;
-    }
-#pragma unroll 2
-    for (; tt < t_end; ++tt) fast_step<DMAX, P, W, false>(sm, sc, tt, R, e, ec, g, kk);
+    for (int tt = t; tt < t_end; ++tt) fast_step<DMAX, P, W, false>(sm, sc, tt, R, e, ec, g, kk);
     if constexpr (WN > 0) fast_phases<DMAX, P, WN>(sm, sc, t_end, q, R, e, ec, g, kk);
 }
 
@@ -296,7 +292,8 @@ __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm,
             ec[p] = ec0f;
             g[p] = 1.0f;
         }
-        fast_phases<DMAX, P, W0>(sm, sc, 0, q, R, e, ec, g, kk);
+        fast_step<DMAX, P, W0, true>(sm, sc, 0, R, e, ec, g, kk);  // q >= 1: step 0 at full width
+        fast_phases<DMAX, P, W0>(sm, sc, 1, q, R, e, ec, g, kk);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (valid[p]) {
