@@ -42,13 +42,18 @@ WORKLOAD = ("grid50: D=2500 sites on a 50x50 grid, Matern nu=1.5 range 0.1 varia
 #   peak = SMs x 128 FP32 lanes x maximum SM clock (lane operations per second,
 #          an FMA counting as one operation).
 #   algorithmic work per Genz step (one lattice coordinate of one point):
-#          ALG_OPS_STEP fixed operations (tent-transformed lattice coordinate,
-#          Phi^{-1}, Phi, running product) + (t + 1) FMAs for the conditional
-#          mean of row t + 1, i.e. q(q+1)/2 FMAs per point of a q-neighbour term.
+#          ALG_OPS_STEP FP32 operations of the formulation the kernel evaluates
+#          -- lattice coordinate and tent map 5 (scale, 1-w, w e, q, product),
+#          Phi^{-1} 14 (p q, map of log2(p q), 10-term polynomial, p - q, scale),
+#          Phi 15 (1 + |z| k, map of t, 9-term polynomial, |z| c, exponent,
+#          t 2^a, 1 - tail) -- plus (t + 1) FMAs for the conditional mean of
+#          row t + 1, i.e. q(q+1)/2 FMAs per point of a q-neighbour term.
+#          Selects, min/max, integer and special-function-unit instructions
+#          are not counted.
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-ALG_OPS_STEP = 32
+ALG_OPS_STEP = 34
 
 
 def parse():
@@ -244,7 +249,9 @@ def run_ours(args):
         total_s = float(t.item())
     value = world * args.steps / total_s
 
-    ms64, genz64, res_fp64, _ = timed(args.fp64_steps, V.FP64, 0)
+    ms64, genz64, res_fp64 = np.zeros(0), np.zeros(0), []
+    if args.fp64_steps > 0:
+        ms64, genz64, res_fp64, _ = timed(args.fp64_steps, V.FP64, 0)
 
     # end to end through the C ABI with pinned host buffers
     sites_h = torch.from_numpy(prob.sites).pin_memory()
@@ -277,10 +284,10 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "wall_s": wall,
-            "fp64": {"value": len(ms64) / (float(ms64.sum()) / 1000.0), "unit": UNIT,
-                     "steps": len(ms64), "p50_ms": float(np.percentile(ms64, 50)),
-                     "p99_ms": float(np.percentile(ms64, 99)),
-                     "genz_kernel_ms": float(np.mean(genz64))},
+            "fp64": ({"value": len(ms64) / (float(ms64.sum()) / 1000.0), "unit": UNIT,
+                      "steps": len(ms64), "p50_ms": float(np.percentile(ms64, 50)),
+                      "p99_ms": float(np.percentile(ms64, 99)),
+                      "genz_kernel_ms": float(np.mean(genz64))} if len(ms64) else None),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "kernel": "genz_kernel (mixed)", "kernel_ms": genz_s * 1000.0,
@@ -300,7 +307,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         lp_o, se_o = O.log_cdf(s, nbr, m, prob.cov, u, N, S, 0)
         t_or = time.perf_counter() - t0
-        lp_m, lp_64 = res_mixed[0][0], res_fp64[0][0]
+        lp_m = res_mixed[0][0]
+        lp_64 = res_fp64[0][0] if res_fp64 else float("nan")
         line["error_vs_oracle"] = {
             "seed": 0, "oracle_log_p": lp_o, "qmc_se": se_o, "oracle_s": t_or,
             "mixed_abs": abs(lp_m - lp_o), "mixed_tol": 1e-4 * max(1.0, abs(lp_o)),
