@@ -149,6 +149,27 @@ typedef struct {
 int vecchia_log_cdf_batch(vecchia_ctx* ctx, const vecchia_problem* probs, int n_probs,
                           int precision, double* log_p, double* std_err, int32_t* status);
 
+/* A plan: a batch prepared once and replayed, for callers that evaluate the
+ * same sites and neighbour lists many times with new covariance parameters or
+ * QMC seeds (a likelihood optimiser, Sec. 4.1, calls the log-CDF at every
+ * parameter value).  vecchia_plan_create validates the batch, keeps its inputs
+ * resident (host arrays are copied once; device arrays are read in place and
+ * must stay valid and unchanged while the plan lives), allocates the plan's
+ * own device and pinned host buffers, runs the batch once and captures its
+ * whole device sequence (parameter upload, shift tables, Genz kernels, the
+ * re-evaluation pass, log-sum, result download) as one CUDA graph.
+ * vecchia_plan_run replays the graph with new seeds and/or covariances
+ * (arrays of n_probs, either may be NULL to keep the previous ones) on the
+ * plan's own stream, ordered after work already queued on the context's
+ * stream, and returns host results like vecchia_log_cdf_batch.  Results are
+ * identical to vecchia_log_cdf_batch on the same inputs. */
+typedef struct vecchia_plan vecchia_plan;
+int vecchia_plan_create(vecchia_ctx* ctx, const vecchia_problem* probs, int n_probs, int precision,
+                        vecchia_plan** plan, int32_t* status);
+int vecchia_plan_run(vecchia_plan* plan, const uint64_t* seeds, const vecchia_cov* covs, double* log_p,
+                     double* std_err, int32_t* status);
+int vecchia_plan_destroy(vecchia_plan* plan);
+
 /* Korobov generating vector g[j] = a^j mod N, j < dim (host array): a in
  * [2, N/2], gcd(a, N) = 1, minimising the weighted P2 criterion over 30
  * dimensions with weights 1/j^2 (ties: smaller a).  N < 4 gives a = 1. */

@@ -80,6 +80,10 @@ def lib():
                                             _vp]
         L.vecchia_log_cdf_batch.argtypes = [_vp, C.POINTER(vecchia_problem), C.c_int, C.c_int, _vp,
                                             _vp, _vp]
+        L.vecchia_plan_create.argtypes = [_vp, C.POINTER(vecchia_problem), C.c_int, C.c_int,
+                                          C.POINTER(_vp), _vp]
+        L.vecchia_plan_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.vecchia_plan_destroy.argtypes = [_vp]
         L.vecchia_lattice.argtypes = [C.c_int64, C.c_int, _vp]
         L.vecchia_shifts.argtypes = [C.c_uint64, C.c_int, C.c_int, _vp]
         L.vecchia_last_error_site.restype = C.c_int64
@@ -270,9 +274,7 @@ def vecchia_log_cdf_terms(ctx, sites_ordered, nbr, m, cov, u, N, S, seed=0, prec
     return lp.value, se.value, terms, num, den
 
 
-def vecchia_log_cdf_batch(ctx, problems, precision=MIXED):
-    """problems: list of dicts with keys sites, nbr, m, cov, u, N, S, seed (arrays all
-    host or all device).  Returns numpy arrays (log_p, std_err, status)."""
+def _problem_array(problems):
     n = len(problems)
     arr = (vecchia_problem * n)()
     keep = []
@@ -283,12 +285,62 @@ def vecchia_log_cdf_batch(ctx, problems, precision=MIXED):
         keep.append((s, uu, nb))
         arr[i] = vecchia_problem(_ptr(s), _ptr(nb), _ptr(uu), s.shape[0], m, int(p["S"]), int(p["N"]),
                                  int(p.get("seed", 0)), make_cov(p["cov"]))
+    return arr, keep
+
+
+def vecchia_log_cdf_batch(ctx, problems, precision=MIXED):
+    """problems: list of dicts with keys sites, nbr, m, cov, u, N, S, seed (arrays all
+    host or all device).  Returns numpy arrays (log_p, std_err, status)."""
+    n = len(problems)
+    arr, keep = _problem_array(problems)
     lp = np.empty(n)
     se = np.empty(n)
     st = np.empty(n, dtype=np.int32)
     _check(lib().vecchia_log_cdf_batch(ctx.handle, arr, n, int(precision), lp.ctypes.data,
                                        se.ctypes.data, st.ctypes.data), "vecchia_log_cdf_batch", ctx)
     return lp, se, st
+
+
+class Plan:
+    """vecchia_plan: a batch kept resident and replayed as a CUDA graph."""
+
+    def __init__(self, ctx, problems, precision=MIXED):
+        self.n = len(problems)
+        arr, self._keep = _problem_array(problems)  # device arrays must outlive the plan
+        self.status = np.empty(self.n, dtype=np.int32)
+        h = _vp()
+        _check(lib().vecchia_plan_create(ctx.handle, arr, self.n, int(precision), C.byref(h),
+                                         self.status.ctypes.data), "vecchia_plan_create", ctx)
+        self.handle = h
+        self.ctx = ctx
+
+    def run(self, seeds=None, covs=None):
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        cv = None
+        if covs is not None:
+            cv = (vecchia_cov * self.n)(*[make_cov(c) for c in covs])
+        lp = np.empty(self.n)
+        se = np.empty(self.n)
+        st = np.empty(self.n, dtype=np.int32)
+        _check(lib().vecchia_plan_run(self.handle, None if sd is None else sd.ctypes.data,
+                                      None if cv is None else C.addressof(cv), lp.ctypes.data,
+                                      se.ctypes.data, st.ctypes.data), "vecchia_plan_run", self.ctx)
+        return lp, se, st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vecchia_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vecchia_plan_create(ctx, problems, precision=MIXED):
+    return Plan(ctx, problems, precision)
 
 
 def vecchia_lattice(N, dim):
