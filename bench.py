@@ -67,8 +67,10 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the error check and cpu_baseline")
     ap.add_argument("--l2-flush-mb", type=int, default=512)
     ap.add_argument("--cpu-sample-sites", type=int, default=160)
-    ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096"],
-                    help="grid50: the headline line; batch4096: the batched workload (its own line)")
+    ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving"],
+                    help="grid50: the headline line; batch4096 / serving: their own lines")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-rates", default="2000,60", help="arrival rates (req/s) to run")
     ap.add_argument("--batch-problems", type=int, default=4096)
     return ap.parse_args()
 
@@ -386,12 +388,52 @@ def run_batch(args):
     ctx.close()
 
 
+def run_serving(args):
+    """The serving workload: Poisson arrivals, D log-uniform in [100, 50000],
+    m in {10, 20, 30}, Matern range along a random walk in [0.05, 0.5], nu in
+    {0.5, 1.5}, sites uniform in the unit square (xy order), N = 2,048 x S = 8,
+    mixed precision, through the continuous-batching loop; one line per rate."""
+    import torch
+    import paper_2007_15195_gb300 as V
+    from paper_2007_15195_gb300 import inputs
+    from paper_2007_15195_gb300.serve import Server, requests_from_stream
+
+    torch.cuda.set_device(0)
+    ctx = V.Context(0)
+    warm = requests_from_stream(inputs.serving_stream(n_requests=16, rate_hz=1e6, workload_seed=99,
+                                                      d_hi=5000))
+    srv = Server(ctx, V.MIXED, hbm_budget_bytes=64 << 30, max_active=512, chunk_sites=4096,
+                 iter_sites=131072)
+    srv.run(warm)
+    for rate in [float(x) for x in args.serve_rates.split(",")]:
+        reqs = requests_from_stream(inputs.serving_stream(n_requests=args.serve_requests, rate_hz=rate))
+        stats = srv.run(reqs)
+        steps = sum(float(np.sum(np.minimum(np.arange(r.D), r.m))) for r in reqs) * 2048 * 8
+        line = {"metric": "Vecchia log-CDF serving: requests/s and p50/p99 latency",
+                "value": stats["throughput_rps"], "unit": "requests/s", "n_gpus": 1,
+                "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "serving: Poisson %.0f req/s, %d requests, D log-uniform [100, 50000], "
+                                       "m in {10,20,30}, Matern nu in {0.5,1.5}, range random walk [0.05,0.5], "
+                                       "N=2048 x S=8, xy order" % (rate, len(reqs)),
+                           "precision": "mixed", "hbm_budget_bytes": srv.budget, "max_active": srv.max_active,
+                           "chunk_sites": srv.chunk, "iter_sites": srv.iter_sites},
+                "offered_rps": rate, "genz_steps_per_s": steps / max(stats["wall_s"], 1e-9)}
+        line.update({k: stats[k] for k in ("completed", "submitted", "ok", "p50_ms", "p99_ms", "wait_p50_ms",
+                                           "wait_p99_ms", "iterations", "wall_s", "peak_resident_bytes")})
+        print(json.dumps(line))
+        sys.stdout.flush()
+    srv.close()
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch4096":
         run_batch(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

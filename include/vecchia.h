@@ -149,6 +149,50 @@ typedef struct {
 int vecchia_log_cdf_batch(vecchia_ctx* ctx, const vecchia_problem* probs, int n_probs,
                           int precision, double* log_p, double* std_err, int32_t* status);
 
+/* ---- building blocks for schedulers (continuous batching) ----------------
+ * The result slot of a problem, in device memory; the layout the library
+ * writes.  status is a vecchia_status; bad_site the first failing ordered site
+ * (INT64_MAX when none). */
+typedef struct {
+    double log_p;
+    double std_err;
+    int64_t bad_site;
+    int32_t status;
+    int32_t reserved;
+} vecchia_result;
+
+/* A range of sites of one problem: the Genz partial means of sites
+ * site_begin .. site_begin + site_count - 1 (all shifts) are written into
+ * num/den (D x S, device), failures into *result (device).  All arrays are
+ * device memory that stays valid until the work has run on the stream. */
+typedef struct {
+    vecchia_problem prob;
+    double* num;
+    double* den;
+    vecchia_result* result;
+    int64_t site_begin;
+    int64_t site_count;
+} vecchia_segment;
+
+/* vecchia_neighbors for device arrays without waiting: queued on the
+ * context's stream (stream-ordered with the other calls) and returning at
+ * once.  sites_ordered and nbr must be device memory. */
+int vecchia_neighbors_async(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, int m,
+                            int32_t* nbr);
+/* Set n result slots to {0, 0, INT64_MAX, VECCHIA_OK} (stream-ordered). */
+int vecchia_result_init(vecchia_ctx* ctx, vecchia_result* results, int n);
+/* Steps a2-a6 for the given site segments of any problems, in one set of
+ * launches on the context's stream; returns without waiting (stream-ordered
+ * with earlier and later calls on the context).  Segments of different
+ * problems, different m, N, S and covariances mix freely; a site's partial
+ * means do not depend on which segments it was launched with.  Invalid
+ * segments make the whole call VECCHIA_ERR_ARG before anything is queued. */
+int vecchia_partials_async(vecchia_ctx* ctx, const vecchia_segment* segs, int n_segs, int precision);
+/* Step a7 for whole problems whose partials are complete (site ranges are
+ * ignored): writes log_p, std_err (and VECCHIA_ERR_NONFINITE) into each
+ * problem's result slot; stream-ordered, returns without waiting. */
+int vecchia_reduce_async(vecchia_ctx* ctx, const vecchia_segment* probs, int n_probs);
+
 /* A plan: a batch prepared once and replayed, for callers that evaluate the
  * same sites and neighbour lists many times with new covariance parameters or
  * QMC seeds (a likelihood optimiser, Sec. 4.1, calls the log-CDF at every

@@ -51,6 +51,15 @@ class vecchia_problem(C.Structure):
                 ("cov", vecchia_cov)]
 
 
+class vecchia_segment(C.Structure):
+    _fields_ = [("prob", vecchia_problem), ("num", C.c_void_p), ("den", C.c_void_p),
+                ("result", C.c_void_p), ("site_begin", C.c_int64), ("site_count", C.c_int64)]
+
+
+# host view of a vecchia_result slot (32 bytes)
+RESULT_DTYPE = np.dtype([("log_p", "<f8"), ("std_err", "<f8"), ("bad_site", "<i8"), ("status", "<i4"),
+                         ("reserved", "<i4")])
+
 _lib = None
 _vp = C.c_void_p
 
@@ -80,6 +89,10 @@ def lib():
                                             _vp]
         L.vecchia_log_cdf_batch.argtypes = [_vp, C.POINTER(vecchia_problem), C.c_int, C.c_int, _vp,
                                             _vp, _vp]
+        L.vecchia_neighbors_async.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp]
+        L.vecchia_result_init.argtypes = [_vp, _vp, C.c_int]
+        L.vecchia_partials_async.argtypes = [_vp, C.POINTER(vecchia_segment), C.c_int, C.c_int]
+        L.vecchia_reduce_async.argtypes = [_vp, C.POINTER(vecchia_segment), C.c_int]
         L.vecchia_plan_create.argtypes = [_vp, C.POINTER(vecchia_problem), C.c_int, C.c_int,
                                           C.POINTER(_vp), _vp]
         L.vecchia_plan_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
@@ -341,6 +354,40 @@ class Plan:
 
 def vecchia_plan_create(ctx, problems, precision=MIXED):
     return Plan(ctx, problems, precision)
+
+
+def vecchia_neighbors_async(ctx, sites_ordered, m, out=None):
+    """Queue the neighbour search for device arrays; returns the (not yet
+    filled) int32 tensor."""
+    s = sites_ordered
+    D = s.shape[0]
+    nbr = out if out is not None else torch.empty((D, max(int(m), 0)), dtype=torch.int32, device=s.device)
+    _check(lib().vecchia_neighbors_async(ctx.handle, _ptr(s), D, int(m), _ptr(nbr) if m > 0 else None),
+           "vecchia_neighbors_async", ctx)
+    return nbr
+
+
+def vecchia_result_init(ctx, results, n):
+    """results: a device tensor holding n 32-byte result slots."""
+    _check(lib().vecchia_result_init(ctx.handle, _ptr(results), int(n)), "vecchia_result_init", ctx)
+
+
+def make_segment(sites, nbr, u, m, cov, N, S, seed, num, den, result_ptr, site_begin, site_count):
+    prob = vecchia_problem(_ptr(sites), _ptr(nbr) if m > 0 else None, _ptr(u), sites.shape[0], int(m),
+                           int(S), int(N), int(seed), make_cov(cov))
+    return vecchia_segment(prob, _ptr(num), _ptr(den), result_ptr, int(site_begin), int(site_count))
+
+
+def vecchia_partials_async(ctx, segments, precision=MIXED):
+    n = len(segments)
+    arr = (vecchia_segment * n)(*segments)
+    _check(lib().vecchia_partials_async(ctx.handle, arr, n, int(precision)), "vecchia_partials_async", ctx)
+
+
+def vecchia_reduce_async(ctx, segments):
+    n = len(segments)
+    arr = (vecchia_segment * n)(*segments)
+    _check(lib().vecchia_reduce_async(ctx.handle, arr, n), "vecchia_reduce_async", ctx)
 
 
 def vecchia_lattice(N, dim):

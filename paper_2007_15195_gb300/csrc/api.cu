@@ -26,6 +26,12 @@ struct vecchia_ctx {
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double genz_ms = 0.0;
+    // asynchronous calls: two pinned parameter buffers used in turn, each
+    // reused only after the upload that last read it has executed
+    void* astage[2] = {nullptr, nullptr};
+    size_t astage_cap[2] = {0, 0};
+    cudaEvent_t astage_ev[2] = {nullptr, nullptr};
+    int astage_i = 0;
 };
 
 namespace vk {
@@ -624,6 +630,59 @@ void plan_free(vecchia_plan* P) {
     delete P;
 }
 
+// ------------------------- asynchronous segment calls ------------------------
+
+// A pinned parameter buffer for an asynchronous call, safe to overwrite now.
+char* async_stage(vecchia_ctx* c, size_t bytes, int* which) {
+    const int k = c->astage_i;
+    c->astage_i ^= 1;
+    if (cudaEventSynchronize(c->astage_ev[k]) != cudaSuccess) cudaGetLastError();
+    if (c->astage_cap[k] < bytes) {
+        if (c->astage[k]) cudaFreeHost(c->astage[k]);
+        c->astage[k] = nullptr;
+        c->astage_cap[k] = 0;
+        const size_t cap = std::max(bytes, (size_t)1 << 16);
+        if (cudaMallocHost(&c->astage[k], cap) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        c->astage_cap[k] = cap;
+    }
+    *which = k;
+    return (char*)c->astage[k];
+}
+
+bool segment_ok(const vecchia_segment& g) {
+    return check_problem(g.prob) == VECCHIA_OK && g.num && g.den && g.result && g.site_begin >= 0 &&
+           g.site_count >= 0 && g.site_begin + g.site_count <= g.prob.D;
+}
+
+void fill_probdev(ProbDev& d, const vecchia_segment& g, uint32_t* lat, char* A, size_t o_delta,
+                  size_t o_dfix, int64_t off) {
+    std::memset(&d, 0, sizeof(d));
+    const auto& p = g.prob;
+    d.sites = p.sites;
+    d.nbr = p.nbr;
+    d.u = p.u;
+    d.num = g.num;
+    d.den = g.den;
+    d.g = lat;
+    d.gfix = lat ? lat + kDim : nullptr;
+    d.delta = (const double*)(A + o_delta) + off;
+    d.dfix = (const uint32_t*)(A + o_dfix) + off;
+    d.D = p.D;
+    d.N = p.N;
+    d.variance = p.cov.variance;
+    d.range = p.cov.range;
+    d.nu = p.cov.nu;
+    d.nugget = p.cov.nugget;
+    d.cov_kind = p.cov.kind;
+    d.m = p.m;
+    d.S = p.S;
+    d.dim = kDim;
+    d.res = (ProbResult*)g.result;
+}
+
 // ------------------------------ host ordering ------------------------------
 
 void quantize_host(const double* s, int64_t D, std::vector<int64_t>& q) {
@@ -740,7 +799,9 @@ int vecchia_create(vecchia_ctx** ctx, int device, void* cuda_stream) {
     if (!c) return VECCHIA_ERR_NOMEM;
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
-    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->astage_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->astage_ev[1], cudaEventDisableTiming) != cudaSuccess) {
         delete c;
         return VECCHIA_ERR_CUDA;
     }
@@ -757,6 +818,10 @@ int vecchia_destroy(vecchia_ctx* c) {
     for (auto& kv : c->lattice_dev) cudaFree(kv.second);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (int k = 0; k < 2; ++k) {
+        if (c->astage[k]) cudaFreeHost(c->astage[k]);
+        if (c->astage_ev[k]) cudaEventDestroy(c->astage_ev[k]);
+    }
     delete c;
     return VECCHIA_OK;
 }
@@ -889,6 +954,22 @@ int vecchia_neighbors(vecchia_ctx* c, const double* sites, int64_t D, int m, int
     return VECCHIA_OK;
 }
 
+int vecchia_neighbors_async(vecchia_ctx* c, const double* sites, int64_t D, int m, int32_t* nbr) {
+    if (!c || !sites || D < 1 || D > INT_MAX / 2 || m < 0) return VECCHIA_ERR_ARG;
+    if (m > VECCHIA_MAX_M) return VECCHIA_ERR_UNSUPPORTED;
+    if (m == 0) return VECCHIA_OK;
+    if (!nbr) return VECCHIA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    int st = ensure_arena(c, vk::knn_scratch_bytes(D));
+    if (st != VECCHIA_OK) return st;
+    const cudaError_t e = vk::launch_knn(sites, D, m, nbr, c->arena, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    return VECCHIA_OK;
+}
+
 int vecchia_log_cdf_terms(vecchia_ctx* c, const double* sites, int64_t D, const int32_t* nbr, int m,
                           vecchia_cov cov, const double* u, int64_t N, int S, uint64_t seed,
                           int precision, double* log_p, double* std_err, double* terms, double* num,
@@ -923,6 +1004,176 @@ int vecchia_log_cdf_batch(vecchia_ctx* c, const vecchia_problem* probs, int n_pr
                           double* log_p, double* std_err, int32_t* status) {
     if (!c || !probs || n_probs < 1 || !log_p || !std_err || !status) return VECCHIA_ERR_ARG;
     return run_problems(c, probs, n_probs, precision, log_p, std_err, status, nullptr, nullptr, nullptr);
+}
+
+int vecchia_result_init(vecchia_ctx* c, vecchia_result* results, int n) {
+    if (!c || n < 0 || (n > 0 && !results)) return VECCHIA_ERR_ARG;
+    if (n == 0) return VECCHIA_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    const cudaError_t e = vk::launch_init_results((ProbResult*)results, n, nullptr, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    return VECCHIA_OK;
+}
+
+int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, int precision) {
+    if (!c || n < 0 || (n > 0 && !segs)) return VECCHIA_ERR_ARG;
+    if (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) return VECCHIA_ERR_ARG;
+    if (n == 0) return VECCHIA_OK;
+    for (int i = 0; i < n; ++i)
+        if (!segment_ok(segs[i])) return VECCHIA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    const bool mixed = precision == VECCHIA_MIXED;
+    int64_t bucket_sites[NB] = {0}, total_sites = 0;
+    int bucket_segs[NB] = {0}, max_S[NB] = {0};
+    std::vector<int> bk(n);
+    std::vector<uint32_t*> lat(n);
+    for (int i = 0; i < n; ++i) {
+        const auto& p = segs[i].prob;
+        bk[i] = vk::bucket_of(p.m + 1);
+        bucket_sites[bk[i]] += segs[i].site_count;
+        bucket_segs[bk[i]] += segs[i].site_count > 0;
+        max_S[bk[i]] = std::max(max_S[bk[i]], p.S);
+        total_sites += segs[i].site_count;
+        lat[i] = lattice_for(c, p.N);
+        if (!lat[i]) return VECCHIA_ERR_NOMEM;
+    }
+    GenzTile tiles[NB];
+    int max_groups = 1;
+    for (int b = 0; b < NB; ++b) {
+        tiles[b] = c->tile_set[mixed][b] ? c->tile[mixed][b] : default_tile(mixed, total_sites, std::max(max_S[b], 2));
+        max_groups = std::max(max_groups, tiles[b].groups);
+    }
+    const int64_t fb_cap = mixed ? std::max<int64_t>(total_sites * max_groups, 1) : 1;
+    Carve dv(nullptr);
+    const size_t o_delta = dv.off;
+    dv.take<double>((size_t)n * vk::kMaxS * kDim);
+    const size_t o_dfix = dv.off;
+    dv.take<uint32_t>((size_t)n * vk::kMaxS * kDim);
+    const size_t o_fbc = dv.off;
+    dv.take<int>(1);
+    const size_t o_fbi = dv.off;
+    dv.take<int2>((size_t)fb_cap);
+    Carve hb(nullptr);
+    const size_t b_probs = hb.off;
+    hb.take<ProbDev>(n);
+    const size_t b_seeds = hb.off;
+    hb.take<uint64_t>(n);
+    const size_t b_S = hb.off;
+    hb.take<int32_t>(n);
+    const size_t b_off = hb.off;
+    hb.take<int64_t>(n);
+    size_t b_segp[NB], b_segb[NB];
+    for (int b = 0; b < NB; ++b) {
+        b_segp[b] = hb.off;
+        hb.take<int>(bucket_segs[b] + 1);
+        b_segb[b] = hb.off;
+        hb.take<int2>(std::max(bucket_segs[b], 1));
+    }
+    const size_t blob_bytes = hb.off;
+    const size_t o_blob = dv.off;
+    dv.take<char>(blob_bytes);
+    int st = ensure_arena(c, dv.off);
+    if (st != VECCHIA_OK) return st;
+    int which = 0;
+    char* H = async_stage(c, blob_bytes, &which);
+    if (!H) return VECCHIA_ERR_NOMEM;
+    char* A = (char*)c->arena;
+    ProbDev* hp = (ProbDev*)(H + b_probs);
+    for (int i = 0; i < n; ++i) {
+        const int64_t off = (int64_t)i * vk::kMaxS * kDim;
+        fill_probdev(hp[i], segs[i], lat[i], A, o_delta, o_dfix, off);
+        ((uint64_t*)(H + b_seeds))[i] = segs[i].prob.seed;
+        ((int32_t*)(H + b_S))[i] = segs[i].prob.S;
+        ((int64_t*)(H + b_off))[i] = off;
+    }
+    for (int b = 0; b < NB; ++b) {
+        int* sp = (int*)(H + b_segp[b]);
+        int2* sb = (int2*)(H + b_segb[b]);
+        int k = 0, run = 0;
+        for (int i = 0; i < n; ++i) {
+            if (bk[i] != b || segs[i].site_count <= 0) continue;
+            sp[k] = run;
+            sb[k] = make_int2(i, (int)segs[i].site_begin);
+            run += (int)segs[i].site_count;
+            ++k;
+        }
+        sp[k] = run;
+    }
+    const cudaStream_t s = c->stream;
+    char* blob = A + o_blob;
+    int* fbc = (int*)(A + o_fbc);
+    cudaError_t e = cudaMemcpyAsync(blob, H, blob_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->astage_ev[which], s);
+    if (e == cudaSuccess) e = vk::launch_init_results(nullptr, 0, fbc, s);
+    if (e == cudaSuccess)
+        e = vk::launch_shifts((const uint64_t*)(blob + b_seeds), (const int32_t*)(blob + b_S),
+                              (const int64_t*)(blob + b_off), n, kDim, (double*)(A + o_delta),
+                              (uint32_t*)(A + o_dfix), s);
+    ProbDev* probs_d = (ProbDev*)(blob + b_probs);
+    for (int b = NB - 1; b >= 0 && e == cudaSuccess; --b) {
+        if (!bucket_sites[b]) continue;
+        e = vk::launch_genz(b, mixed, tiles[b], probs_d, (const int*)(blob + b_segp[b]),
+                            (const int2*)(blob + b_segb[b]), bucket_segs[b], (int)bucket_sites[b], nullptr,
+                            fbc, (int2*)(A + o_fbi), max_S[b], s);
+    }
+    if (mixed && e == cudaSuccess)
+        e = vk::launch_genz_fallback(probs_d, fbc, (int2*)(A + o_fbi), (int)fb_cap, nullptr, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    return VECCHIA_OK;
+}
+
+int vecchia_reduce_async(vecchia_ctx* c, const vecchia_segment* probs, int n) {
+    if (!c || n < 0 || (n > 0 && !probs)) return VECCHIA_ERR_ARG;
+    if (n == 0) return VECCHIA_OK;
+    for (int i = 0; i < n; ++i)
+        if (!segment_ok(probs[i])) return VECCHIA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    int64_t scratch = 0, max_slices = 0;
+    for (int i = 0; i < n; ++i) {
+        scratch += vk::logsum_scratch(probs[i].prob.D, probs[i].prob.S);
+        max_slices = std::max(max_slices, vk::logsum_slices(probs[i].prob.D));
+    }
+    Carve dv(nullptr);
+    const size_t o_scr = dv.off;
+    dv.take<double>(scratch);
+    Carve hb(nullptr);
+    const size_t b_probs = hb.off;
+    hb.take<ProbDev>(n);
+    const size_t b_off = hb.off;
+    hb.take<int64_t>(n);
+    const size_t blob_bytes = hb.off;
+    const size_t o_blob = dv.off;
+    dv.take<char>(blob_bytes);
+    int st = ensure_arena(c, dv.off);
+    if (st != VECCHIA_OK) return st;
+    int which = 0;
+    char* H = async_stage(c, blob_bytes, &which);
+    if (!H) return VECCHIA_ERR_NOMEM;
+    char* A = (char*)c->arena;
+    int64_t run = 0;
+    for (int i = 0; i < n; ++i) {
+        fill_probdev(((ProbDev*)(H + b_probs))[i], probs[i], nullptr, A, 0, 0, 0);
+        ((int64_t*)(H + b_off))[i] = run;
+        run += vk::logsum_scratch(probs[i].prob.D, probs[i].prob.S);
+    }
+    const cudaStream_t s = c->stream;
+    char* blob = A + o_blob;
+    cudaError_t e = cudaMemcpyAsync(blob, H, blob_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->astage_ev[which], s);
+    if (e == cudaSuccess)
+        e = vk::launch_logsum((const ProbDev*)(blob + b_probs), n, (int)max_slices, nullptr, nullptr,
+                              (double*)(A + o_scr), (const int64_t*)(blob + b_off), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    return VECCHIA_OK;
 }
 
 int vecchia_plan_create(vecchia_ctx* c, const vecchia_problem* probs, int n_probs, int precision,

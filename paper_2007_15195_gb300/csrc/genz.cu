@@ -594,8 +594,9 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(DMAX, P, MODE))
         __syncthreads();
         if (threadIdx.x == 0) {
             if (sm.bad) {
-                atomicMin((unsigned long long*)&results[item.x].bad_site, (unsigned long long)site);
-                results[item.x].status = (sm.bad == 1) ? VECCHIA_ERR_NOT_PD : VECCHIA_ERR_ARG;
+                ProbResult* R = Pd.res ? Pd.res : &results[item.x];
+                atomicMin((unsigned long long*)&R->bad_site, (unsigned long long)site);
+                R->status = (sm.bad == 1) ? VECCHIA_ERR_NOT_PD : VECCHIA_ERR_ARG;
             } else if (MODE == kModeFast && sm.flag && fallback_items) {
                 const int pos = atomicAdd(fallback_count, 1);
                 fallback_items[pos] = item;
@@ -687,7 +688,7 @@ __global__ void __launch_bounds__(32) logsum_final_kernel(const ProbDev* __restr
         ss += l * l;
     }
     if (lane == 0) {
-        ProbResult& R = results[pi];
+        ProbResult& R = Pd.res ? *Pd.res : results[pi];
         R.log_p = log_p;
         R.std_err = sqrt(ss / ((double)S * (double)(S - 1)));
         if (R.status == VECCHIA_OK && !(isfinite(log_p) && isfinite(R.std_err)))

@@ -28,6 +28,8 @@ inline int bucket_of(int d) {
     return -1;
 }
 
+struct ProbResult;
+
 // One log-CDF problem as the device sees it (all pointers device memory).
 struct ProbDev {
     const double* sites;   // D x 2, ordered
@@ -46,6 +48,7 @@ struct ProbDev {
     int32_t m;
     int32_t S;
     int32_t dim;           // row stride of delta / dfix
+    ProbResult* res;       // result slot owned by the caller (segment calls), or nullptr
 };
 
 // Result slot of a problem, written by the log-sum kernel.
