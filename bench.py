@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the error check and cpu_baseline")
     ap.add_argument("--l2-flush-mb", type=int, default=512)
     ap.add_argument("--cpu-sample-sites", type=int, default=160)
-    ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving"],
+    ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving", "large"],
                     help="grid50: the headline line; batch4096 / serving: their own lines")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-rates", default="2000,60", help="arrival rates (req/s) to run")
@@ -426,6 +426,68 @@ def run_serving(args):
     ctx.close()
 
 
+def run_large(args):
+    """The large workload: D = 100,000 uniform sites, exact maxmin order,
+    Matern nu in {0.5, 1.5} with range 0.05, u ~ U[0, 2], m = 30,
+    N = 8,192 x S = 16: ordering (host), neighbour search and the mixed
+    log-CDF timed separately; the FP64 path on a 10,000-site ordered prefix
+    (its per-step rate scales to the full problem)."""
+    import torch
+    import paper_2007_15195_gb300 as V
+    from paper_2007_15195_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = V.Context(0)
+    V.vecchia_set_timing(ctx, True)
+    for nu in (1.5, 0.5):
+        prob = inputs.large(nu=nu)
+        t0 = time.perf_counter()
+        perm = V.vecchia_order(None, prob.sites, "maxmin")
+        t_order = time.perf_counter() - t0
+        s, u = V.vecchia_apply_order(None, perm, prob.sites, prob.u)
+        ds, du = torch.from_numpy(s).to(dev), torch.from_numpy(u).to(dev)
+        nbr = V.vecchia_neighbors(ctx, ds, prob.m)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            nbr = V.vecchia_neighbors(ctx, ds, prob.m)
+        t_knn = (time.perf_counter() - t0) / 3
+        V.vecchia_log_cdf(ctx, ds, nbr, prob.m, prob.cov, du, prob.N, prob.S, 99, V.MIXED)
+        ms, genz = [], []
+        for k in range(max(args.steps // 10, 2)):
+            t0 = time.perf_counter()
+            lp, se = V.vecchia_log_cdf(ctx, ds, nbr, prob.m, prob.cov, du, prob.N, prob.S, k, V.MIXED)
+            ms.append(1000.0 * (time.perf_counter() - t0))
+            genz.append(V.vecchia_genz_time_ms(ctx))
+        K = 10_000
+        pre = (ds[:K].contiguous(), du[:K].contiguous(), nbr[:K].contiguous())
+        t0 = time.perf_counter()
+        lp64, se64 = V.vecchia_log_cdf(ctx, pre[0], pre[2], prob.m, prob.cov, pre[1], prob.N, prob.S, 0, V.FP64)
+        t64 = time.perf_counter() - t0
+        q = np.minimum(np.arange(prob.D), prob.m).astype(np.float64)
+        steps = float(q.sum()) * prob.N * prob.S
+        steps_pre = float(q[:K].sum()) * prob.N * prob.S
+        work = float(np.sum(q * ALG_OPS_STEP + q * (q + 1) / 2.0)) * prob.N * prob.S
+        peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+        genz_s = float(np.median(genz)) / 1000.0
+        line = {"metric": "Vecchia log-CDF evals/s, large workload (D=100,000, m=30)",
+                "value": 1000.0 / float(np.mean(ms)), "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "large: D=100000 uniform, maxmin, Matern nu=%g range 0.05, u~U[0,2], "
+                                       "m=30, N=8192 x S=16" % nu, "precision": "mixed"},
+                "ms_per_eval": float(np.mean(ms)), "log_p": lp, "std_err": se, "order_s": t_order,
+                "neighbors_ms": 1000.0 * t_knn, "genz_steps": steps,
+                "fp64_prefix": {"sites": K, "s": t64, "log_p": lp64,
+                                "est_full_s": t64 * steps / steps_pre},
+                "roofline": {"bound": "alu", "achieved": work / genz_s / 1e12, "peak": peak / 1e12,
+                             "unit": "TFLOP/s", "frac": work / genz_s / peak, "traffic": None,
+                             "kernel": "genz_kernel (mixed)", "kernel_ms": genz_s * 1000.0}}
+        print(json.dumps(line))
+        sys.stdout.flush()
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -434,6 +496,8 @@ def main():
         run_batch(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "large":
+        run_large(args)
     else:
         run_ours(args)
 

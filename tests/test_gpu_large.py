@@ -1,0 +1,70 @@
+"""The large workload at full size: D = 100,000 sites uniform in the unit
+square, exact maxmin order, Matern nu in {0.5, 1.5} with range 0.05,
+u ~ U[0, 2], m = 30, N = 8,192 x S = 16.  The full mixed-precision
+evaluation is checked term by term on sampled sites against the oracle's
+one-site evaluation; the FP64 path on an ordered prefix (itself a valid
+problem: every neighbour of site i < K is among the first K sites)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_15195_gb300 import binding as B
+from paper_2007_15195_gb300 import inputs
+
+from _prep import mixed_tol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def large_ordered():
+    prob = inputs.large(nu=1.5)
+    perm = B.vecchia_order(None, prob.sites, "maxmin")
+    s, u = B.vecchia_apply_order(None, perm, prob.sites, prob.u)
+    return prob, s, u
+
+
+@pytest.mark.parametrize("nu", [1.5, 0.5])
+def test_large_mixed_terms_against_oracle(ctx, large_ordered, nu):
+    import torch
+    prob, s, u = large_ordered
+    cov = (prob.cov[0], prob.cov[1], prob.cov[2], nu, 0.0)
+    ds, du = torch.from_numpy(s).cuda(), torch.from_numpy(u).cuda()
+    nbr = B.vecchia_neighbors(ctx, ds, prob.m)
+    lp, se, terms, num, den = B.vecchia_log_cdf_terms(ctx, ds, nbr, prob.m, cov, du, prob.N, prob.S, 0,
+                                                      B.MIXED)
+    assert np.isfinite(lp) and lp < 0
+    terms = terms.cpu().numpy()
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([[0, 1, 2, 15, 30, 31, 32], rng.integers(33, prob.D, 40)]))
+    nb_h = nbr.cpu().numpy()
+    for i in idx[:12]:
+        assert np.array_equal(nb_h[i], O.neighbors_of(s, int(i), prob.m))
+    onum, oden = O.vecchia_partials(s, nb_h, prob.m, cov, u, prob.N, prob.S, 0, idx=idx)
+    t_or = np.log(onum.mean(1)) - np.log(oden.mean(1))
+    per_term = mixed_tol(lp) / prob.D
+    assert np.max(np.abs(terms[idx] - t_or)) <= per_term, np.max(np.abs(terms[idx] - t_or))
+
+
+def test_large_fp64_on_ordered_prefix(ctx, large_ordered):
+    prob, s, u = large_ordered
+    K = 3000
+    sp, up = np.ascontiguousarray(s[:K]), np.ascontiguousarray(u[:K])
+    nbr = B.vecchia_neighbors(ctx, sp, prob.m)
+    full_nbr = B.vecchia_neighbors(ctx, s, prob.m)
+    assert np.array_equal(nbr, full_nbr[:K])
+    lp, se, terms, num, den = B.vecchia_log_cdf_terms(ctx, sp, nbr, prob.m, prob.cov, up, prob.N, prob.S, 3,
+                                                      B.FP64)
+    idx = np.array([0, 1, 29, 30, 31, 500, 1777, K - 1])
+    onum, oden = O.vecchia_partials(sp, nbr, prob.m, prob.cov, up, prob.N, prob.S, 3, idx=idx)
+    assert np.allclose(num[idx], onum, rtol=1e-10, atol=0)
+    assert np.allclose(den[idx], oden, rtol=1e-10, atol=0)
+    mlp, mse = B.vecchia_log_cdf(ctx, sp, nbr, prob.m, prob.cov, up, prob.N, prob.S, 3, B.MIXED)
+    assert abs(mlp - lp) <= mixed_tol(lp)
