@@ -23,7 +23,6 @@ constexpr float kLn2 = 0.693147180559945309f;
 constexpr float kLn4 = 1.38629436111989062f;
 constexpr float kSqrt2 = 1.41421356237309505f;
 constexpr float kTinyZ = -9.0f;   // Phi(-9) ~ 2^-62.5: below, carry log2 Phi instead
-constexpr float kFloor = 2.35098870e-38f;  // 2^-125: r q stays a normal float
 
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -94,9 +93,10 @@ __device__ __forceinline__ void phi_pair(float z, float& e, float& ec, bool& tin
     if (tiny) le2 = lg2(t) + a;
 }
 
-// Phi(z) and 1 - Phi(z) without the log-space output (e flushes to 0 below 2^-126).
+// Phi(z) and 1 - Phi(z) without the log-space output (e flushes to 0 below
+// 2^-126; beyond the fitted |z| <= 38 the exponent only grows more negative).
 __device__ __forceinline__ void phi_pair_fast(float z, float& e, float& ec) {
-    const float az = fminf(fabsf(z), kZmax);
+    const float az = fabsf(z);
     const float t = rcp(fmaf(az, kKt, 1.0f));
     const float a = fmaf(__fmul_rn(az, -0.5f * kLog2e), az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
     const float tail = __fmul_rn(t, ex2(a));
@@ -107,17 +107,17 @@ __device__ __forceinline__ void phi_pair_fast(float z, float& e, float& ec) {
 
 // f_s(w) = sqrt(2) erfinv(y)/y for w >= 8 (sqrt(w) pieces).
 __device__ __forceinline__ float finv_tail(float w) {
-    const float s = sqrt_approx(w);
+    const float s = sqrt_approx(w);  // w = +inf gives s = +inf: the last piece at its end
     if (s < 6.0f) return horner(kINV2C, fmaf(s, kINV2A, kINV2B));  // w in [8, 36)
     if (s < 11.4017543f) return horner(kINV3C, fmaf(s, kINV3A, kINV3B));
     return horner(kINV4C, fmaf(fminf(s, 26.4575131f), kINV4A, kINV4B));
 }
 
-// Phi^{-1}(p) given p and q = 1 - p (both >= 0).
+// Phi^{-1}(p) given p and q = 1 - p (both >= 0).  w depends on p q only and
+// the sign on p - q, so no min/max is needed; p q = 0 (or below the normal
+// range) gives L = -inf and the far-tail piece at its end, a finite value.
 __device__ __forceinline__ float phiinv_pq(float p, float q) {
-    const float r = fmaxf(fminf(p, q), kFloor);
-    const float o = fmaxf(p, q);
-    const float L = lg2(__fmul_rn(r, o));  // w = -ln 2 (L + 2)
+    const float L = lg2(__fmul_rn(p, q));  // w = -ln 2 (L + 2)
     float f;
     if (L > kINV1Lmin)
         f = horner(kINV1C, fmaf(L, kINV1LA, kINV1LB));
