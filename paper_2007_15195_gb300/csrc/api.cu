@@ -265,17 +265,18 @@ uint32_t* lattice_for(vecchia_ctx* c, int64_t N) {
     return d;
 }
 
-// Built-in tile: 4 warps, one point per lane, and enough shift groups (a power
-// of two, so that S = 2^k splits evenly) for ~4096 CTA items.
-GenzTile default_tile(bool mixed, int64_t total_sites, int max_S) {
+// Built-in tile: 4 warps; two points per lane for blocks of up to 21 variables
+// (registers allow the second independent chain there), one above; enough
+// shift groups (a power of two, so S = 2^k splits evenly) for ~4096 CTA items,
+// but never fewer shifts per item than warps (a warp without a unit idles).
+GenzTile default_tile(bool mixed, int64_t total_sites, int max_S, int bucket) {
     GenzTile t;
     t.warps = 4;
-    t.points = 1;
+    t.points = (mixed && vk::kDmaxBuckets[bucket] <= 21) ? 2 : 1;
     t.slices = 1;
     int g = 1;
-    while (g < max_S && (int64_t)g * total_sites < 4096) g *= 2;
+    while (g < max_S && (int64_t)g * total_sites < 4096 && max_S / (2 * g) >= t.warps) g *= 2;
     t.groups = g;
-    (void)mixed;
     return t;
 }
 
@@ -354,7 +355,7 @@ int prepare(vecchia_ctx* c, const vecchia_problem* probs, int n, int precision, 
     int max_groups = 1;
     for (int b = 0; b < NB; ++b) {
         B.tiles[b] = c->tile_set[B.mixed][b] ? c->tile[B.mixed][b]
-                                             : default_tile(B.mixed, B.total_sites, std::max(B.max_S[b], 2));
+                                             : default_tile(B.mixed, B.total_sites, std::max(B.max_S[b], 2), b);
         max_groups = std::max(max_groups, B.tiles[b].groups);
     }
     B.fb_cap = B.mixed ? B.total_sites * max_groups : 0;
@@ -1043,7 +1044,8 @@ int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, i
     GenzTile tiles[NB];
     int max_groups = 1;
     for (int b = 0; b < NB; ++b) {
-        tiles[b] = c->tile_set[mixed][b] ? c->tile[mixed][b] : default_tile(mixed, total_sites, std::max(max_S[b], 2));
+        tiles[b] = c->tile_set[mixed][b] ? c->tile[mixed][b]
+                                         : default_tile(mixed, total_sites, std::max(max_S[b], 2), b);
         max_groups = std::max(max_groups, tiles[b].groups);
     }
     const int64_t fb_cap = mixed ? std::max<int64_t>(total_sites * max_groups, 1) : 1;

@@ -92,12 +92,13 @@ extern "C" int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const doub
     const bool mixed = precision == VECCHIA_MIXED;
     constexpr int kDim = vk::kMaxDim;
 
-    // tile: the built-in rule of vecchia_log_cdf (4 warps, one point per lane,
-    // power-of-two shift groups for ~4096 CTA items)
-    int groups = 1;
-    while (groups < S && (int64_t)groups * D < 4096) groups *= 2;
-    const vk::GenzTile tile{4, 1, 1, groups};
+    // tile: the built-in rule of vecchia_log_cdf (4 warps; two points per lane
+    // for blocks of up to 21 variables; power-of-two shift groups for ~4096 CTA
+    // items, never fewer shifts per item than warps)
     const int bucket = vk::bucket_of(m + 1);
+    int groups = 1;
+    while (groups < S && (int64_t)groups * D < 4096 && S / (2 * groups) >= 4) groups *= 2;
+    const vk::GenzTile tile{4, (mixed && vk::kDmaxBuckets[bucket] <= 21) ? 2 : 1, 1, groups};
 
     // scratch layout (every offset a multiple of 256 bytes)
     size_t off = 0;

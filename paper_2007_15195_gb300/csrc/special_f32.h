@@ -116,13 +116,16 @@ __device__ __forceinline__ float finv_tail(float w) {
 // Phi^{-1}(p) given p and q = 1 - p (both >= 0).  w depends on p q only and
 // the sign on p - q, so no min/max is needed; p q = 0 (or below the normal
 // range) gives L = -inf and the far-tail piece at its end, a finite value.
+// Every lane evaluates the central piece; the tail pieces (p q < 2^-13.5,
+// rarely reached) run only when a warp vote says some lane needs them.
 __device__ __forceinline__ float phiinv_pq(float p, float q) {
     const float L = lg2(__fmul_rn(p, q));  // w = -ln 2 (L + 2)
-    float f;
-    if (L > kINV1Lmin)
-        f = horner(kINV1C, fmaf(L, kINV1LA, kINV1LB));
-    else
-        f = finv_tail(__fmul_rn(-kLn2, __fadd_rn(L, 2.0f)));
+    float f = horner(kINV1C, fmaf(L, kINV1LA, kINV1LB));
+    const bool tail = !(L > kINV1Lmin);
+    if (__any_sync(__activemask(), tail)) {  // among the lanes executing this call
+        const float ft = finv_tail(__fmul_rn(-kLn2, __fadd_rn(L, 2.0f)));
+        f = tail ? ft : f;
+    }
     return __fmul_rn(__fsub_rn(p, q), f);
 }
 
