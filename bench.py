@@ -67,11 +67,12 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the error check and cpu_baseline")
     ap.add_argument("--l2-flush-mb", type=int, default=512)
     ap.add_argument("--cpu-sample-sites", type=int, default=160)
-    ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving", "large"],
-                    help="grid50: the headline line; batch4096 / serving: their own lines")
+    ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving", "large", "mixture"],
+                    help="grid50: the headline line; the others print their own lines")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-rates", default="2000,60", help="arrival rates (req/s) to run")
     ap.add_argument("--batch-problems", type=int, default=4096)
+    ap.add_argument("--mixture-nodes", type=int, default=16)
     return ap.parse_args()
 
 
@@ -488,6 +489,54 @@ def run_large(args):
     ctx.close()
 
 
+def run_mixture(args):
+    """The scale-mixture CDF G(x) = int Phi_D(x/r) dF_R(r) (Sec. 4) on the
+    grid50 sites (D = 2,500, Matern nu = 1.5, m = 20, N = 4,096 x S = 16),
+    beta = 0.5, gamma = 1 (the paper fixes gamma = 1), 16 quadrature nodes:
+    one step is one vecchia_mixture_log_cdf call from host arrays (a batch of
+    16 Vecchia log-CDFs)."""
+    import torch
+    import paper_2007_15195_gb300 as V
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = V.Context(0)
+    V.vecchia_set_timing(ctx, True)
+    prob = prepare_workload(args.m)
+    perm = V.vecchia_order(None, prob.sites, prob.order)
+    s, u = V.vecchia_apply_order(None, perm, prob.sites, prob.u)
+    nbr = V.vecchia_neighbors(ctx, s, prob.m)
+    n = args.mixture_nodes
+    run = lambda seed: V.vecchia_mixture_log_cdf(ctx, s, nbr, prob.m, prob.cov, u, prob.N, prob.S, seed,
+                                                 beta=0.5, gamma=1.0, n_nodes=n, precision=V.MIXED)
+    for k in range(max(args.warmup, 3)):
+        run(10_000 + k)
+    ms, genz = [], []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        lg, se = run(k)
+        ms.append(1000.0 * (time.perf_counter() - t0))
+        genz.append(V.vecchia_genz_time_ms(ctx))
+    ms = np.array(ms)
+    work = n * alg_ops(prob.D, prob.m, prob.N, prob.S)
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    genz_s = float(np.median(genz)) / 1000.0
+    line = {"metric": "scale-mixture log G evals/s (D=2500, m=20, %d nodes)" % n,
+            "value": 1000.0 / float(ms.mean()), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "mixture: grid50 sites, Matern nu=1.5 range 0.1, m=20, N=4096 x S=16, "
+                                   "beta=0.5 gamma=1, %d nodes" % n, "precision": "mixed",
+                       "step": "vecchia_mixture_log_cdf from host arrays (e2e)"},
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "log_g": lg, "std_err": se,
+            "roofline": {"bound": "alu", "achieved": work / genz_s / 1e12, "peak": peak / 1e12,
+                         "unit": "TFLOP/s", "frac": work / genz_s / peak, "traffic": None,
+                         "kernel": "genz_kernel (mixed)", "kernel_ms": genz_s * 1000.0}}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -498,6 +547,8 @@ def main():
         run_serving(args)
     elif args.workload == "large":
         run_large(args)
+    elif args.workload == "mixture":
+        run_mixture(args)
     else:
         run_ours(args)
 

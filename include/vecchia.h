@@ -214,6 +214,26 @@ int vecchia_plan_run(vecchia_plan* plan, const uint64_t* seeds, const vecchia_co
                      double* std_err, int32_t* status);
 int vecchia_plan_destroy(vecchia_plan* plan);
 
+/* The scale-mixture CDF of Sec. 4 (Eq. model01-model03): X = R W with W the
+ * Gaussian process of `cov` and R independent with
+ *   F_R(r) = 1 - exp(-gamma (r^beta - 1) / beta),  r >= 1, beta > 0,
+ *   F_R(r) = 1 - r^(-gamma)                            (beta = 0, the limit),
+ * G(x) = P(X < x) = int Phi_D(x / r; Sigma) dF_R(r).  With v = F_R(r) the
+ * integral is over [0, 1]; the substitution v = 1 - (1 - t)^4 removes the
+ * singularity of F_R^{-1} at v = 1, and an n_nodes-point Gauss-Legendre rule
+ * in t (quadrature error of log G about 1e-6 or less at 16 nodes for
+ * beta >= 0.2, gamma >= 1, |x| <= 4 in one dimension) together with
+ * Phi_D(x / r; Sigma) = Phi_D(x; r^2 Sigma) turn it into n_nodes Vecchia
+ * log-CDFs on the same sites and neighbour lists with the covariance scaled by
+ * r^2, evaluated as one batch (common random numbers across nodes).
+ * log_g = log sum_q w_q P_q; std_err bounds the QMC error of log_g by full
+ * correlation of the nodes' errors.  beta >= 0, gamma > 0, 1 <= n_nodes <= 256;
+ * other arguments as for vecchia_log_cdf (x are the centred thresholds). */
+int vecchia_mixture_log_cdf(vecchia_ctx* ctx, const double* sites_ordered, int64_t D,
+                            const int32_t* nbr, int m, vecchia_cov cov, const double* x, int64_t N,
+                            int S, uint64_t seed, double beta, double gamma, int n_nodes,
+                            int precision, double* log_g, double* std_err);
+
 /* Korobov generating vector g[j] = a^j mod N, j < dim (host array): a in
  * [2, N/2], gcd(a, N) = 1, minimising the weighted P2 criterion over 30
  * dimensions with weights 1/j^2 (ties: smaller a).  N < 4 gives a = 1. */

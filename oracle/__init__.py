@@ -308,3 +308,43 @@ def num_threads():
 def set_threads(n):
     """Threads for later calls (OpenMP reads the variable at first parallel region)."""
     os.environ["OMP_NUM_THREADS"] = str(int(n))
+
+
+# ---- scale mixture (Sec. 4, Eq. model01-model03) ----------------------------
+def mixing_quantile(v, beta, gamma):
+    """r = F_R^{-1}(v) for F_R(r) = 1 - exp(-gamma (r^beta - 1)/beta), r >= 1
+    (Eq. model02, beta > 0) and its beta -> 0 limit 1 - r^(-gamma) (the
+    printed "1 - r^gamma" read with the exponent's sign restored)."""
+    L = -np.log1p(-np.asarray(v, dtype=np.float64))
+    if beta > 0:
+        return (1.0 + beta * L / gamma) ** (1.0 / beta)
+    return np.exp(L / gamma)
+
+
+def mixture_nodes(n_nodes):
+    """Nodes v_q in (0, 1) and weights of the rule for int_0^1 f(v) dv: the
+    substitution v = 1 - (1 - t)^4 (dv = 4 (1 - t)^3 dt), then Gauss-Legendre
+    in t on [0, 1].  The substitution flattens the singularity of F_R^{-1} at
+    v = 1."""
+    t, w = np.polynomial.legendre.leggauss(n_nodes)
+    t = 0.5 * (t + 1.0)
+    w = 0.5 * w * 4.0 * (1.0 - t) ** 3
+    return 1.0 - (1.0 - t) ** 4, w
+
+
+def mixture_log_cdf(sites, nbr, m, cov, x, N, S, seed, beta, gamma, n_nodes):
+    """log G(x), G(x) = int Phi_D(x / r; Sigma) dF_R(r) (Eq. model03) =
+    int_0^1 Phi_D(x / F_R^{-1}(v); Sigma) dv by the rule of mixture_nodes,
+    each node's Vecchia log-CDF with the covariance scaled by r^2
+    (Phi_D(x/r; Sigma) = Phi_D(x; r^2 Sigma)); written with numpy on top of
+    log_cdf."""
+    v, w = mixture_nodes(n_nodes)
+    kind, var, rng_, nu, nug = cov
+    terms = []
+    for vq, wq in zip(v, w):
+        r = float(mixing_quantile(vq, beta, gamma))
+        lp, _ = log_cdf(sites, nbr, m, (kind, var * r * r, rng_, nu, nug * r * r), x, N, S, seed)
+        terms.append(np.log(wq) + lp)
+    terms = np.array(terms)
+    mx = terms.max()
+    return float(mx + np.log(np.sum(np.exp(terms - mx))))

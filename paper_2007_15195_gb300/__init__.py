@@ -10,7 +10,7 @@ call does, and fails if it has not been built.
 from .binding import (COV_EXPONENTIAL, COV_MATERN, FP64, MIXED, ORDER_IDENTITY, ORDER_MAXMIN,
                       ORDER_XY, Context, Plan, VecchiaError, make_cov, vecchia_create, vecchia_destroy,
                       vecchia_apply_order, vecchia_genz_time_ms, vecchia_last_error_site, vecchia_lattice,
-                      vecchia_log_cdf, vecchia_log_cdf_batch, vecchia_log_cdf_terms,
+                      vecchia_log_cdf, vecchia_log_cdf_batch, vecchia_log_cdf_terms, vecchia_mixture_log_cdf,
                       vecchia_neighbors, vecchia_order, vecchia_plan_create, vecchia_reset_tiles, vecchia_set_tile,
                       vecchia_set_timing, vecchia_shifts)
 
@@ -18,6 +18,6 @@ __all__ = [
     "COV_EXPONENTIAL", "COV_MATERN", "FP64", "MIXED", "ORDER_IDENTITY", "ORDER_MAXMIN", "ORDER_XY",
     "Context", "Plan", "VecchiaError", "vecchia_plan_create", "make_cov", "vecchia_create", "vecchia_destroy",
     "vecchia_apply_order", "vecchia_genz_time_ms", "vecchia_last_error_site", "vecchia_lattice", "vecchia_log_cdf",
-    "vecchia_log_cdf_batch", "vecchia_log_cdf_terms", "vecchia_neighbors", "vecchia_order",
+    "vecchia_log_cdf_batch", "vecchia_log_cdf_terms", "vecchia_mixture_log_cdf", "vecchia_neighbors", "vecchia_order",
     "vecchia_reset_tiles", "vecchia_set_tile", "vecchia_set_timing", "vecchia_shifts",
 ]

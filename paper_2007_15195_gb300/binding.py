@@ -97,6 +97,10 @@ def lib():
                                           C.POINTER(_vp), _vp]
         L.vecchia_plan_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.vecchia_plan_destroy.argtypes = [_vp]
+        L.vecchia_mixture_log_cdf.argtypes = [_vp, _vp, C.c_int64, _vp, C.c_int, vecchia_cov, _vp,
+                                              C.c_int64, C.c_int, C.c_uint64, C.c_double, C.c_double,
+                                              C.c_int, C.c_int, C.POINTER(C.c_double),
+                                              C.POINTER(C.c_double)]
         L.vecchia_lattice.argtypes = [C.c_int64, C.c_int, _vp]
         L.vecchia_shifts.argtypes = [C.c_uint64, C.c_int, C.c_int, _vp]
         L.vecchia_last_error_site.restype = C.c_int64
@@ -254,6 +258,18 @@ def vecchia_log_cdf(ctx, sites_ordered, nbr, m, cov, u, N, S, seed=0, precision=
                                  _ptr(uu), int(N), int(S), C.c_uint64(int(seed)), int(precision),
                                  C.byref(lp), C.byref(se)), "vecchia_log_cdf", ctx)
     return lp.value, se.value
+
+
+def vecchia_mixture_log_cdf(ctx, sites_ordered, nbr, m, cov, x, N, S, seed=0, beta=0.5, gamma=1.0,
+                            n_nodes=16, precision=MIXED):
+    s, xx = _f64(sites_ordered), _f64(x)
+    nb = _i32(nbr) if m > 0 else None
+    lg, se = C.c_double(), C.c_double()
+    _check(lib().vecchia_mixture_log_cdf(ctx.handle, _ptr(s), s.shape[0], _ptr(nb), int(m), make_cov(cov),
+                                         _ptr(xx), int(N), int(S), C.c_uint64(int(seed)), float(beta),
+                                         float(gamma), int(n_nodes), int(precision), C.byref(lg),
+                                         C.byref(se)), "vecchia_mixture_log_cdf", ctx)
+    return lg.value, se.value
 
 
 def vecchia_log_cdf_noalloc(device, stream, sites_ordered, nbr, m, cov, u, N, S, seed=0,

@@ -684,6 +684,44 @@ void fill_probdev(ProbDev& d, const vecchia_segment& g, uint32_t* lat, char* A, 
     d.res = (ProbResult*)g.result;
 }
 
+// ----------------------- scale-mixture CDF (Sec. 4) -------------------------
+
+// Gauss-Legendre rule on [0, 1]: Newton's method on the Legendre polynomial
+// P_n from the Chebyshev-like first guesses, weights 2/((1-x^2) P_n'(x)^2)
+// (Golub & Welsch give the same rule; this is the classical root iteration).
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int k = 1; k <= n; ++k) {  // P_k(z) by the three-term recurrence
+                const double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            const double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        const double wt = 2.0 / ((1.0 - z * z) * dp * dp);
+        x[i] = 0.5 * (1.0 - z);
+        x[n - 1 - i] = 0.5 * (1.0 + z);
+        w[i] = w[n - 1 - i] = 0.5 * wt;
+    }
+}
+
+// r = F_R^{-1}(v) for F_R(r) = 1 - exp(-gamma (r^beta - 1)/beta), r >= 1
+// (beta > 0), and its beta -> 0 limit F_R(r) = 1 - r^(-gamma), written in
+// terms of L = -log(1 - v) >= 0.
+double mixing_radius(double L, double beta, double gamma) {
+    if (beta > 0.0) return std::pow(1.0 + beta * L / gamma, 1.0 / beta);
+    return std::exp(L / gamma);
+}
+
 // ------------------------------ host ordering ------------------------------
 
 void quantize_host(const double* s, int64_t D, std::vector<int64_t>& q) {
@@ -999,6 +1037,59 @@ int vecchia_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, const int32_
     if (!log_p || !std_err) return VECCHIA_ERR_ARG;
     return vecchia_log_cdf_terms(c, sites, D, nbr, m, cov, u, N, S, seed, precision, log_p, std_err,
                                  nullptr, nullptr, nullptr);
+}
+
+int vecchia_mixture_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, const int32_t* nbr, int m,
+                            vecchia_cov cov, const double* x, int64_t N, int S, uint64_t seed,
+                            double beta, double gamma, int n_nodes, int precision, double* log_g,
+                            double* std_err) {
+    if (!c || !log_g || !std_err) return VECCHIA_ERR_ARG;
+    if (!(beta >= 0.0) || !(gamma > 0.0) || !std::isfinite(beta) || !std::isfinite(gamma) || n_nodes < 1 ||
+        n_nodes > 256)
+        return VECCHIA_ERR_ARG;
+    *log_g = NAN;
+    *std_err = NAN;
+    // G = int_0^1 Phi_D(x / F_R^{-1}(v)) dv.  F_R^{-1} is singular at v = 1,
+    // so v = 1 - (1 - t)^4 (dv = 4 (1 - t)^3 dt) flattens the integrand there
+    // before the Gauss-Legendre rule in t: L = -log(1 - v) = -4 log(1 - t).
+    std::vector<double> t, w;
+    gauss_legendre01(n_nodes, t, w);
+    std::vector<vecchia_problem> probs(n_nodes);
+    for (int q = 0; q < n_nodes; ++q) {
+        const double omt = 1.0 - t[q];
+        w[q] *= 4.0 * omt * omt * omt;
+        const double r = mixing_radius(-4.0 * std::log1p(-t[q]), beta, gamma);
+        vecchia_problem& p = probs[q];
+        p.sites = sites;
+        p.nbr = nbr;
+        p.u = x;
+        p.D = D;
+        p.m = m;
+        p.S = S;
+        p.N = N;
+        p.seed = seed;
+        p.cov = cov;
+        p.cov.variance = cov.variance * r * r;  // Phi_D(x / r; Sigma) = Phi_D(x; r^2 Sigma)
+        p.cov.nugget = cov.nugget * r * r;
+    }
+    std::vector<double> lp(n_nodes), se(n_nodes);
+    std::vector<int32_t> st(n_nodes);
+    int rc = run_problems(c, probs.data(), n_nodes, precision, lp.data(), se.data(), st.data(), nullptr,
+                          nullptr, nullptr);
+    if (rc != VECCHIA_OK) return rc;
+    for (int q = 0; q < n_nodes; ++q)
+        if (st[q] != VECCHIA_OK) return st[q];
+    // log G = log sum_q w_q P_q, in a fixed order with the largest term factored out
+    double mx = -INFINITY;
+    for (int q = 0; q < n_nodes; ++q) mx = std::max(mx, std::log(w[q]) + lp[q]);
+    double sum = 0.0;
+    for (int q = 0; q < n_nodes; ++q) sum += std::exp(std::log(w[q]) + lp[q] - mx);
+    *log_g = mx + std::log(sum);
+    // the nodes share shifts (correlated errors): bound by full correlation
+    double seb = 0.0;
+    for (int q = 0; q < n_nodes; ++q) seb += std::exp(std::log(w[q]) + lp[q] - *log_g) * se[q];
+    *std_err = seb;
+    return VECCHIA_OK;
 }
 
 int vecchia_log_cdf_batch(vecchia_ctx* c, const vecchia_problem* probs, int n_probs, int precision,

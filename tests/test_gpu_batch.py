@@ -127,3 +127,19 @@ def test_autotune_picks_and_caches_a_tile(ctx, batch256, tmp_path):
     B.vecchia_reset_tiles(ctx)
     lp_default = B.vecchia_log_cdf_batch(ctx, sub, B.MIXED)[0]
     assert np.array_equal(lp_tuned, lp_default)  # slices = 1: bit-identical
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
+def test_mixture_log_cdf_against_oracle(ctx, prec):
+    """Sec. 4 scale mixture: n_nodes Vecchia log-CDFs with scaled covariance in
+    one batch, combined by the quadrature rule."""
+    prob = inputs.small_random(150, 23, m=10, N=512, S=4)
+    perm = O.order(prob.sites, O.ORDER_MAXMIN)
+    s, u = prob.sites[perm], prob.u[perm] + 1.0
+    nbr = O.neighbors(s, 10)
+    ref = O.mixture_log_cdf(s, nbr, 10, prob.cov, u, 512, 4, 5, 0.6, 1.2, 10)
+    lg, se = B.vecchia_mixture_log_cdf(ctx, s, nbr, 10, prob.cov, u, 512, 4, 5, beta=0.6, gamma=1.2,
+                                       n_nodes=10, precision=prec)
+    tol = 1e-10 * abs(ref) if prec == B.FP64 else mixed_tol(ref)
+    assert abs(lg - ref) <= tol, (lg, ref)
+    assert se > 0
