@@ -27,6 +27,21 @@ _i64p = C.POINTER(C.c_int64)
 _u32p = C.POINTER(C.c_uint32)
 
 
+COV_ANISO_EXP = 2
+
+
+class CovT(C.Structure):
+    """vref_cov_t: kind, variance, range, nu, nugget, angle, aspect."""
+    _fields_ = [("kind", C.c_int), ("variance", C.c_double), ("range", C.c_double), ("nu", C.c_double),
+                ("nugget", C.c_double), ("angle", C.c_double), ("aspect", C.c_double)]
+
+
+def _cov_t(cov):
+    """A covariance tuple (kind, variance, range, nu, nugget[, angle, aspect])."""
+    c = tuple(cov) + (0.0, 1.0)[len(cov) - 5:] if len(cov) < 7 else tuple(cov)
+    return CovT(int(c[0]), *[float(x) for x in c[1:7]])
+
+
 class OracleError(RuntimeError):
     def __init__(self, status, where, site=-1):
         super().__init__("oracle %s returned %d%s" % (where, status,
@@ -79,6 +94,18 @@ def lib():
                                    _dp, _dp, _i64p]
         L.vref_full_genz.argtypes = [_dp, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_double,
                                      C.c_double, _dp, C.c_int64, C.c_int, C.c_uint64, _dp, _dp]
+        L.vref_genz_sums_c.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_int64, C.c_int, _u32p, _dp,
+                                       C.c_int, _dp, _dp]
+        L.vref_group_cond_nearest.argtypes = [_dp, C.c_int64, C.c_int, C.c_int, C.c_int, _i32p, _i32p]
+        L.vref_group_cond_random.argtypes = [C.c_int64, C.c_int, C.c_int, C.c_uint64, C.c_int, _i32p,
+                                             _i32p]
+        L.vref_aniso_h.restype = C.c_double
+        L.vref_aniso_h.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
+        L.vref_cov_matrix_t.argtypes = [_dp, C.c_int64, C.POINTER(CovT), _dp]
+        L.vref_grouped_partials.argtypes = [_dp, C.c_int64, C.c_int, _i32p, C.c_int, C.POINTER(CovT), _dp,
+                                            C.c_int64, C.c_int, C.c_uint64, _dp, _dp, _i64p]
+        L.vref_grouped_log_cdf.argtypes = [_dp, C.c_int64, C.c_int, _i32p, C.c_int, C.POINTER(CovT), _dp,
+                                           C.c_int64, C.c_int, C.c_uint64, _dp, _dp, _dp, _i64p]
         L.vref_num_threads.restype = C.c_int
         L.vref_num_threads.argtypes = []
         _lib = L
@@ -298,6 +325,94 @@ def full_genz(sites, cov, u, N, S, seed):
     se = C.c_double()
     _check(lib().vref_full_genz(_ptr(s, _dp), s.shape[0], *_cov_args(cov), _ptr(u, _dp), N, S,
                                 C.c_uint64(seed), C.byref(lp), C.byref(se)), "full_genz")
+    return lp.value, se.value
+
+
+# ---- general terms: joint groups, conditioning sets (Sec. 3.2) ---------------
+def genz_sums_c(Sigma, u, c, N, S, g, delta):
+    Sig = _f64(Sigma)
+    d = Sig.shape[0]
+    u = _f64(u)
+    g = np.ascontiguousarray(g, dtype=np.uint32)
+    delta = _f64(delta)
+    dim = delta.shape[1] if delta.ndim == 2 else 1
+    num = np.zeros(S)
+    den = np.zeros(S)
+    _check(lib().vref_genz_sums_c(d, c, _ptr(Sig, _dp), _ptr(u, _dp), N, S, _ptr(g, _u32p),
+                                  _ptr(delta, _dp), dim, _ptr(num, _dp), _ptr(den, _dp)), "genz_sums_c")
+    return num, den
+
+
+def group_cond_nearest(sites, p, m, cmax):
+    s = _f64(sites).reshape(-1, 2)
+    D = s.shape[0]
+    G = (D + p - 1) // p
+    cond = np.full((G, max(cmax, 1)), -1, dtype=np.int32)
+    cnt = np.zeros(G, dtype=np.int32)
+    _check(lib().vref_group_cond_nearest(_ptr(s, _dp), D, p, m, cmax, _ptr(cond, _i32p), _ptr(cnt, _i32p)),
+           "group_cond_nearest")
+    return cond[:, :cmax], cnt
+
+
+def group_cond_random(D, p, kk, seed, cmax):
+    G = (D + p - 1) // p
+    cond = np.full((G, max(cmax, 1)), -1, dtype=np.int32)
+    cnt = np.zeros(G, dtype=np.int32)
+    _check(lib().vref_group_cond_random(D, p, kk, C.c_uint64(seed), cmax, _ptr(cond, _i32p),
+                                        _ptr(cnt, _i32p)), "group_cond_random")
+    return cond[:, :cmax], cnt
+
+
+def aniso_h(dx, dy, angle, aspect):
+    return lib().vref_aniso_h(float(dx), float(dy), float(angle), float(aspect))
+
+
+def cov_matrix_t(sites, cov):
+    s = _f64(sites).reshape(-1, 2)
+    n = s.shape[0]
+    out = np.zeros((n, n))
+    cv = _cov_t(cov)
+    _check(lib().vref_cov_matrix_t(_ptr(s, _dp), n, C.byref(cv), _ptr(out, _dp)), "cov_matrix_t")
+    return out
+
+
+def grouped_partials(sites, p, cond, cov, u, N, S, seed):
+    s = _f64(sites).reshape(-1, 2)
+    D = s.shape[0]
+    G = (D + p - 1) // p
+    cd = np.ascontiguousarray(cond, dtype=np.int32).reshape(G, -1)
+    cmax = cd.shape[1]
+    num = np.zeros((G, S))
+    den = np.zeros((G, S))
+    bad = C.c_int64(-1)
+    cv = _cov_t(cov)
+    st = lib().vref_grouped_partials(_ptr(s, _dp), D, p, _ptr(cd, _i32p) if cmax else None, cmax,
+                                     C.byref(cv), _ptr(_f64(u), _dp), N, S, C.c_uint64(seed),
+                                     _ptr(num, _dp), _ptr(den, _dp), C.byref(bad))
+    _check(st, "grouped_partials", bad.value)
+    return num, den
+
+
+def grouped_log_cdf(sites, p, cond, cov, u, N, S, seed, return_terms=False):
+    """log P ~ sum_k [log Phi(u_{C_k, G_k}) - log Phi(u_{C_k})] over the groups
+    G_k of p consecutive ordered sites and their conditioning sets C_k (rows
+    of cond, ascending, -1 padded)."""
+    s = _f64(sites).reshape(-1, 2)
+    D = s.shape[0]
+    G = (D + p - 1) // p
+    cd = np.ascontiguousarray(cond, dtype=np.int32).reshape(G, -1)
+    cmax = cd.shape[1]
+    lp = C.c_double()
+    se = C.c_double()
+    terms = np.zeros(G)
+    bad = C.c_int64(-1)
+    cv = _cov_t(cov)
+    st = lib().vref_grouped_log_cdf(_ptr(s, _dp), D, p, _ptr(cd, _i32p) if cmax else None, cmax,
+                                    C.byref(cv), _ptr(_f64(u), _dp), N, S, C.c_uint64(seed), C.byref(lp),
+                                    C.byref(se), _ptr(terms, _dp), C.byref(bad))
+    _check(st, "grouped_log_cdf", bad.value)
+    if return_terms:
+        return lp.value, se.value, terms
     return lp.value, se.value
 
 

@@ -416,13 +416,14 @@ static int cmp_i32(const void* pa, const void* pb) {
     return (a < b) ? -1 : (a > b);
 }
 
-/* The q smallest (d^2, j) keys among j < i, then listed ascending in j. */
-static void neighbors_one(const int64_t* q, int64_t i, int m, int32_t* out) {
-    const int64_t cnt = (i < m) ? i : m;
+/* The min(m, lim) smallest (d^2, j) keys of site i among j < lim, then listed
+ * ascending in j (out has m entries, -1 padded). */
+static void neighbors_lim(const int64_t* q, int64_t i, int64_t lim, int m, int32_t* out) {
+    const int64_t cnt = (lim < m) ? lim : m;
     int64_t* kd = (int64_t*)malloc(sizeof(int64_t) * (size_t)(cnt + 1));
     int32_t* kj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt + 1));
     int64_t n = 0;
-    for (int64_t j = 0; j < i && cnt > 0; ++j) {
+    for (int64_t j = 0; j < lim && cnt > 0; ++j) {
         const int64_t d2 = qd2(q, i, j);
         /* j ascending, so an equal d^2 never displaces an earlier entry */
         if (n == cnt && !(d2 < kd[n - 1])) continue;
@@ -440,6 +441,11 @@ static void neighbors_one(const int64_t* q, int64_t i, int m, int32_t* out) {
     for (int r = 0; r < m; ++r) out[r] = (r < n) ? kj[r] : -1;
     free(kd);
     free(kj);
+}
+
+/* N_i: the min(m, i) nearest previously ordered sites (Sec. 2.1). */
+static void neighbors_one(const int64_t* q, int64_t i, int m, int32_t* out) {
+    neighbors_lim(q, i, i, m, out);
 }
 
 int vref_neighbors_of(const double* sites, int64_t D, int64_t i, int m, int32_t* out) {
@@ -737,5 +743,266 @@ int vref_full_genz(const double* sites, int64_t D, int cov_kind, double variance
         *se = rse;
     }
     free(Sig);
+    return st;
+}
+
+/* ======================================================================== */
+/* General terms: joint groups, general conditioning sets (Sec. 3.2)        */
+/* ======================================================================== */
+
+int vref_genz_sums_c(int d, int c, const double* Sigma, const double* u, int64_t N, int S,
+                     const uint32_t* g, const double* delta, int dim, double* num, double* den) {
+    if (d < 1 || c < 0 || c > d - 1 || N < 1 || S < 1 || dim < d - 1 || !Sigma || !u || !num || !den)
+        return VREF_ERR_ARG;
+    if (d > 1 && (!g || !delta)) return VREF_ERR_ARG;
+    double* L = (double*)malloc(sizeof(double) * (size_t)d * d);
+    double* y = (double*)malloc(sizeof(double) * (size_t)(d > 1 ? d - 1 : 1));
+    if (!L || !y) {
+        free(L);
+        free(y);
+        return VREF_ERR_ARG;
+    }
+    const int st = vref_cholesky(d, Sigma, L);
+    if (st != VREF_OK) {
+        free(L);
+        free(y);
+        return st;
+    }
+    double e0, ec0;
+    phi_pair(u[0] / L[0], &e0, &ec0);
+    for (int s = 0; s < S; ++s) {
+        if (d == 1) { /* c = 0: the one-variable CDF, no lattice coordinate */
+            num[s] = e0;
+            den[s] = 1.0;
+            continue;
+        }
+        neumaier_t acc_num = {0.0, 0.0}, acc_den = {0.0, 0.0};
+        for (int64_t k = 0; k < N; ++k) {
+            double e = e0, ec = ec0, f = 1.0, fc = 1.0;
+            for (int t = 0; t + 1 < d; ++t) {
+                f *= e; /* f = e_0 ... e_t */
+                if (t + 1 == c) fc = f; /* the c-dim CDF sample of the leading block */
+                const uint64_t r = ((uint64_t)k * (uint64_t)g[t]) % (uint64_t)N;
+                double x = (double)r / (double)N + delta[(int64_t)s * dim + t];
+                if (x >= 1.0) x -= 1.0;
+                const double a = fabs(2.0 * x - 1.0);
+                const double w = 1.0 - a;
+                y[t] = vref_Phiinv_pq(w * e, a + w * ec);
+                double acc = u[t + 1];
+                for (int j = 0; j <= t; ++j) acc = fma(-L[(t + 1) * d + j], y[j], acc);
+                phi_pair(acc / L[(t + 1) * d + (t + 1)], &e, &ec);
+            }
+            neumaier_add(&acc_num, f * e);
+            if (c > 0) neumaier_add(&acc_den, fc);
+        }
+        num[s] = (acc_num.sum + acc_num.comp) / (double)N;
+        den[s] = (c > 0) ? (acc_den.sum + acc_den.comp) / (double)N : 1.0;
+    }
+    free(L);
+    free(y);
+    return VREF_OK;
+}
+
+static int cmp_i32_asc(const void* pa, const void* pb) {
+    const int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    return (a < b) ? -1 : (a > b);
+}
+
+/* sort ascending and drop repeats; returns the new length */
+static int sort_unique(int32_t* v, int n) {
+    qsort(v, (size_t)n, sizeof(int32_t), cmp_i32_asc);
+    int w = 0;
+    for (int r = 0; r < n; ++r)
+        if (w == 0 || v[r] != v[w - 1]) v[w++] = v[r];
+    return w;
+}
+
+int vref_group_cond_nearest(const double* sites, int64_t D, int p, int m, int cmax, int32_t* cond,
+                            int32_t* count) {
+    if (D < 1 || p < 1 || m < 0 || cmax < 0 || !sites || !count || (cmax > 0 && !cond))
+        return VREF_ERR_ARG;
+    const int64_t G = (D + p - 1) / p;
+    int64_t* q = (int64_t*)malloc(sizeof(int64_t) * 2 * (size_t)D);
+    if (!q) return VREF_ERR_ARG;
+    vref_quantize(sites, D, q);
+    int st = VREF_OK;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < G; ++k) {
+        const int64_t i0 = k * p, i1 = (i0 + p < D) ? i0 + p : D;
+        const int n_all = (int)(i1 - i0) * (m > 0 ? m : 1);
+        int32_t* all = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_all);
+        int32_t* one = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+        int n = 0;
+        for (int64_t i = i0; i < i1 && m > 0; ++i) {
+            neighbors_lim(q, i, i0, m, one); /* among the sites before the group */
+            for (int r = 0; r < m; ++r)
+                if (one[r] >= 0) all[n++] = one[r];
+        }
+        n = sort_unique(all, n);
+        if (n > cmax) {
+#pragma omp critical
+            st = VREF_ERR_ARG;
+        } else {
+            for (int r = 0; r < cmax; ++r) cond[k * cmax + r] = (r < n) ? all[r] : -1;
+            count[k] = n;
+        }
+        free(all);
+        free(one);
+    }
+    free(q);
+    return st;
+}
+
+int vref_group_cond_random(int64_t D, int p, int kk, uint64_t seed, int cmax, int32_t* cond,
+                           int32_t* count) {
+    if (D < 1 || D > 0x7fffffff || p < 1 || kk < 0 || kk > cmax || !count || (cmax > 0 && !cond))
+        return VREF_ERR_ARG;
+    const int64_t G = (D + p - 1) / p;
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    int32_t* set = (int32_t*)malloc(sizeof(int32_t) * (size_t)(kk > 0 ? kk : 1));
+    if (!set) return VREF_ERR_ARG;
+    for (int64_t k = 0; k < G; ++k) {
+        const int64_t n = k * p; /* previously ordered sites */
+        const int take = (int)((kk < n) ? kk : n);
+        /* Floyd's sampling of `take` distinct indices from [0, n): for
+         * j = n - take .. n - 1 draw t uniform in [0, j]; keep t unless it
+         * is already in the set, else keep j. */
+        int have = 0;
+        for (int r = 0; r < take; ++r) {
+            const int64_t j = n - take + r;
+            const uint32_t ctr[4] = {(uint32_t)k, (uint32_t)r, 0x52C5u, (uint32_t)((uint64_t)k >> 32)};
+            uint32_t o[4];
+            vref_philox4x32_10(ctr, key, o);
+            const int32_t t = (int32_t)(((uint64_t)o[0] * (uint64_t)(j + 1)) >> 32);
+            int dup = 0;
+            for (int a = 0; a < have; ++a)
+                if (set[a] == t) dup = 1;
+            set[have++] = dup ? (int32_t)j : t;
+        }
+        qsort(set, (size_t)have, sizeof(int32_t), cmp_i32_asc);
+        for (int r = 0; r < cmax; ++r) cond[k * cmax + r] = (r < have) ? set[r] : -1;
+        count[k] = have;
+    }
+    free(set);
+    return VREF_OK;
+}
+
+double vref_aniso_h(double dx, double dy, double angle, double aspect) {
+    /* Omega = (s_i - s_j)^T R(angle)^{-1} diag(1, aspect), h^2 = Omega Omega^T (Sec. 4.1) */
+    const double c = cos(angle), s = sin(angle);
+    const double o1 = dx * c - dy * s;
+    const double o2 = aspect * (dx * s + dy * c);
+    return sqrt(o1 * o1 + o2 * o2);
+}
+
+static int check_cov_t(const vref_cov_t* cv) {
+    if (cv->kind == VREF_COV_ANISO_EXP)
+        return cv->variance > 0.0 && cv->range > 0.0 && cv->nugget >= 0.0 && isfinite(cv->angle) &&
+               cv->aspect > 0.0;
+    return check_cov(cv->kind, cv->variance, cv->range, cv->nu, cv->nugget);
+}
+
+int vref_cov_matrix_t(const double* sites, int64_t n, const vref_cov_t* cv, double* Sigma) {
+    if (!check_cov_t(cv)) return VREF_ERR_ARG;
+    if (cv->kind != VREF_COV_ANISO_EXP)
+        return vref_cov_matrix(sites, n, cv->kind, cv->variance, cv->range, cv->nu, cv->nugget, Sigma);
+    for (int64_t a = 0; a < n; ++a) {
+        for (int64_t c = 0; c < n; ++c) {
+            const double h = vref_aniso_h(sites[2 * a] - sites[2 * c], sites[2 * a + 1] - sites[2 * c + 1],
+                                          cv->angle, cv->aspect);
+            double v = cv->variance * exp(-h / cv->range);
+            if (a == c) v += cv->nugget;
+            Sigma[a * n + c] = v;
+        }
+    }
+    return VREF_OK;
+}
+
+int vref_grouped_partials(const double* sites, int64_t D, int p, const int32_t* cond, int cmax,
+                          const vref_cov_t* cv, const double* u, int64_t N, int S, uint64_t seed,
+                          double* num, double* den, int64_t* bad_term) {
+    if (D < 1 || p < 1 || cmax < 0 || N < 1 || S < 1 || !sites || !u || !num || !den || !cv)
+        return VREF_ERR_ARG;
+    if (cmax > 0 && !cond) return VREF_ERR_ARG;
+    if (!check_cov_t(cv)) return VREF_ERR_ARG;
+    const int64_t G = (D + p - 1) / p;
+    const int dim = (cmax + p - 1 > 0) ? cmax + p - 1 : 1;
+    uint32_t* g = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)dim);
+    double* delta = (double*)malloc(sizeof(double) * (size_t)S * dim);
+    if (!g || !delta) {
+        free(g);
+        free(delta);
+        return VREF_ERR_ARG;
+    }
+    int st = vref_lattice(N, dim, g);
+    if (st == VREF_OK) st = vref_shifts(seed, S, dim, delta);
+    int64_t first_bad = -1;
+    if (st == VREF_OK) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t k = 0; k < G; ++k) {
+            const int64_t i0 = k * p, i1 = (i0 + p < D) ? i0 + p : D;
+            int c = 0;
+            while (c < cmax && cond[k * cmax + c] >= 0) ++c;
+            const int d = c + (int)(i1 - i0);
+            int64_t* b = (int64_t*)malloc(sizeof(int64_t) * (size_t)d);
+            double* bs = (double*)malloc(sizeof(double) * 2 * (size_t)d);
+            double* bu = (double*)malloc(sizeof(double) * (size_t)d);
+            double* Sig = (double*)malloc(sizeof(double) * (size_t)d * d);
+            int ok = b && bs && bu && Sig;
+            /* block (C_k ascending, then the group's sites): the conditioning
+             * CDF is the leading c-dim block of the joint one */
+            for (int a = 0; ok && a < c; ++a) {
+                b[a] = cond[k * cmax + a];
+                if (b[a] >= i0 || (a > 0 && b[a] <= b[a - 1])) ok = 0;
+            }
+            for (int a = c; ok && a < cmax; ++a)
+                if (cond[k * cmax + a] >= 0) ok = 0;
+            int lst = VREF_ERR_ARG;
+            if (ok) {
+                for (int a = c; a < d; ++a) b[a] = i0 + (a - c);
+                for (int a = 0; a < d; ++a) {
+                    bs[2 * a] = sites[2 * b[a]];
+                    bs[2 * a + 1] = sites[2 * b[a] + 1];
+                    bu[a] = u[b[a]];
+                }
+                lst = vref_cov_matrix_t(bs, d, cv, Sig);
+                if (lst == VREF_OK)
+                    lst = vref_genz_sums_c(d, c, Sig, bu, N, S, g, delta, dim, num + k * S, den + k * S);
+            }
+            if (lst != VREF_OK) {
+#pragma omp critical
+                {
+                    if (first_bad < 0 || k < first_bad) first_bad = k;
+                    if (st == VREF_OK || lst == VREF_ERR_NOT_PD) st = lst;
+                }
+            }
+            free(b);
+            free(bs);
+            free(bu);
+            free(Sig);
+        }
+    }
+    if (bad_term) *bad_term = first_bad;
+    free(g);
+    free(delta);
+    return st;
+}
+
+int vref_grouped_log_cdf(const double* sites, int64_t D, int p, const int32_t* cond, int cmax,
+                         const vref_cov_t* cv, const double* u, int64_t N, int S, uint64_t seed,
+                         double* log_p, double* se, double* terms, int64_t* bad_term) {
+    if (D < 1 || p < 1 || S < 2) return VREF_ERR_ARG;
+    const int64_t G = (D + p - 1) / p;
+    double* num = (double*)malloc(sizeof(double) * (size_t)G * S);
+    double* den = (double*)malloc(sizeof(double) * (size_t)G * S);
+    if (!num || !den) {
+        free(num);
+        free(den);
+        return VREF_ERR_ARG;
+    }
+    int st = vref_grouped_partials(sites, D, p, cond, cmax, cv, u, N, S, seed, num, den, bad_term);
+    if (st == VREF_OK) st = vref_vecchia_reduce(G, S, num, den, log_p, se, terms);
+    free(num);
+    free(den);
     return st;
 }

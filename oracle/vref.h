@@ -29,7 +29,16 @@ extern "C" {
 #endif
 
 enum { VREF_OK = 0, VREF_ERR_ARG = -1, VREF_ERR_NOT_PD = -4 };
-enum { VREF_COV_EXPONENTIAL = 0, VREF_COV_MATERN = 1 };
+enum { VREF_COV_EXPONENTIAL = 0, VREF_COV_MATERN = 1, VREF_COV_ANISO_EXP = 2 };
+
+/* A covariance function: exponential sigma^2 exp(-h/rho); Matern (nu in
+ * {0.5, 1.5, 2.5}); or the anisotropic exponential of Sec. 4.1, whose h is
+ * the Mahalanobis distance with rotation `angle` and aspect ratio `aspect`.
+ * The nugget is added on the diagonal. */
+typedef struct {
+    int kind;
+    double variance, range, nu, nugget, angle, aspect;
+} vref_cov_t;
 enum { VREF_ORDER_XY = 0, VREF_ORDER_MAXMIN = 1, VREF_ORDER_IDENTITY = 2 };
 
 /* ---- univariate normal ------------------------------------------------- */
@@ -136,6 +145,37 @@ int vref_full_genz(const double* sites, int64_t D, int cov_kind, double variance
 
 /* Number of OpenMP threads the partials loop uses. */
 int vref_num_threads(void);
+
+/* ---- general terms: joint groups and conditioning sets (Sec. 3.2) ------- */
+/* As vref_genz_sums for the d-dim block, except that den[s] is the sample mean
+ * of the product of the first c conditional probabilities: the c-dim CDF of
+ * the leading block (0 <= c <= d-1; c = 0 gives den = 1). */
+int vref_genz_sums_c(int d, int c, const double* Sigma, const double* u, int64_t N, int S,
+                     const uint32_t* g, const double* delta, int dim, double* num, double* den);
+/* Groups k = 0..ceil(D/p)-1 of p consecutive ordered sites [k p, k p + p).
+ * Nearest conditioning (Sec. 3.2, first method): the union of the min(m, k p)
+ * nearest sites before the group of each group member, ascending; cond is
+ * G x cmax (-1 padded), count[k] its length; ERR_ARG if a union exceeds cmax. */
+int vref_group_cond_nearest(const double* sites, int64_t D, int p, int m, int cmax, int32_t* cond,
+                            int32_t* count);
+/* Random conditioning (Sec. 3.2, second and third methods, kk = m or p m): a
+ * uniform subset of min(kk, k p) sites before group k by Floyd's algorithm,
+ * draw r of group k an integer in [0, j] from Philox4x32-10 with key = seed,
+ * counter = (k lo32, r, 0x52C5, k hi32): floor(word0 (j + 1) / 2^32). */
+int vref_group_cond_random(int64_t D, int p, int kk, uint64_t seed, int cmax, int32_t* cond,
+                           int32_t* count);
+/* Mahalanobis distance of Sec. 4.1 for the offset (dx, dy). */
+double vref_aniso_h(double dx, double dy, double angle, double aspect);
+int vref_cov_matrix_t(const double* sites, int64_t n, const vref_cov_t* cv, double* Sigma);
+/* Per group k: the joint CDF of (C_k ascending, group sites) and the CDF of
+ * C_k from one Genz run (num, den G x S); terms on the log scale as in
+ * vref_vecchia_reduce.  Lattice and shifts for dim = cmax + p - 1. */
+int vref_grouped_partials(const double* sites, int64_t D, int p, const int32_t* cond, int cmax,
+                          const vref_cov_t* cv, const double* u, int64_t N, int S, uint64_t seed,
+                          double* num, double* den, int64_t* bad_term);
+int vref_grouped_log_cdf(const double* sites, int64_t D, int p, const int32_t* cond, int cmax,
+                         const vref_cov_t* cv, const double* u, int64_t N, int S, uint64_t seed,
+                         double* log_p, double* se, double* terms, int64_t* bad_term);
 
 #ifdef __cplusplus
 }
