@@ -53,17 +53,23 @@ typedef enum {
 
 typedef enum {
     VECCHIA_COV_EXPONENTIAL = 0, /* variance * exp(-h / range)            (Sec. 3, Sec. 4.1) */
-    VECCHIA_COV_MATERN = 1       /* Rasmussen-Williams Matern, nu in {0.5, 1.5, 2.5} */
+    VECCHIA_COV_MATERN = 1,      /* Rasmussen-Williams Matern, nu in {0.5, 1.5, 2.5} */
+    VECCHIA_COV_ANISO_EXP = 2    /* variance * exp(-h / range), h the Mahalanobis distance of
+                                    Sec. 4.1: Omega = (s_i - s_j)^T R(angle)^{-1} diag(1, aspect),
+                                    h^2 = Omega Omega^T */
 } vecchia_cov_kind;
 
-/* Isotropic covariance C(h) of the spatial process; nugget adds to the
- * diagonal (0 for none).  nu is read for VECCHIA_COV_MATERN only. */
+/* Covariance C(s_i, s_j) of the spatial process; nugget adds to the diagonal
+ * (0 for none).  nu is read for VECCHIA_COV_MATERN only; angle (radians) and
+ * aspect (> 0) for VECCHIA_COV_ANISO_EXP only. */
 typedef struct {
     int32_t kind;
     double variance;
     double range;
     double nu;
     double nugget;
+    double angle;
+    double aspect;
 } vecchia_cov;
 
 typedef enum {
@@ -71,8 +77,8 @@ typedef enum {
     VECCHIA_MIXED = 1  /* FP64 covariance, Cholesky and sums; FP32 Genz integrand */
 } vecchia_precision;
 
-/* Largest conditioning-set size m of this build (blocks of <= 32 variables). */
-#define VECCHIA_MAX_M 31
+/* Largest conditioning-set size m of this build (terms of <= 64 variables). */
+#define VECCHIA_MAX_M 63
 /* Largest number of random shifts S per problem. */
 #define VECCHIA_MAX_S 64
 
@@ -104,7 +110,7 @@ int vecchia_apply_order(vecchia_ctx* ctx, const int32_t* perm, const double* sit
  * previously ordered sites, |N_i| = min(m, i-1)).  On GPU: grid-bucketed
  * integer search on quantised coordinates, q = floor((x - xmin) * 2^30 /
  * extent); ties in squared distance go to the smaller index.  nbr is D x m
- * int32 (host or device), each row ascending, padded with -1.  0 <= m <= 31. */
+ * int32 (host or device), each row ascending, padded with -1.  0 <= m <= 63. */
 int vecchia_neighbors(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, int m, int32_t* nbr);
 
 /* Steps a2-a7 -- the Vecchia log-CDF (Eq. vecchia-cdf) with Genz QMC on a
@@ -127,10 +133,12 @@ int vecchia_log_cdf_terms(vecchia_ctx* ctx, const double* sites_ordered, int64_t
                           int S, uint64_t seed, int precision, double* log_p, double* std_err,
                           double* terms, double* num, double* den);
 
-/* One problem of a batch: the arguments of vecchia_log_cdf. */
+/* One problem of a batch: the arguments of vecchia_log_cdf, or, with
+ * group = p >= 1, of vecchia_grouped_log_cdf (nbr then holds the
+ * ceil(D/p) x m conditioning rows of the groups and m is cmax). */
 typedef struct {
     const double* sites;  /* D x 2, ordered */
-    const int32_t* nbr;   /* D x m */
+    const int32_t* nbr;   /* D x m (group 0) or ceil(D/p) x m (group p) */
     const double* u;      /* D */
     int64_t D;
     int32_t m;
@@ -138,6 +146,8 @@ typedef struct {
     int64_t N;
     uint64_t seed;
     vecchia_cov cov;
+    int32_t group;        /* 0: one term per site (Eq. vecchia-cdf); p: joint groups of p sites */
+    int32_t reserved;
 } vecchia_problem;
 
 /* Many independent problems in one set of launches (the terms of every
@@ -149,9 +159,46 @@ typedef struct {
 int vecchia_log_cdf_batch(vecchia_ctx* ctx, const vecchia_problem* probs, int n_probs,
                           int precision, double* log_p, double* std_err, int32_t* status);
 
+/* ---- joint groups and general conditioning sets (Sec. 3.2) ---------------
+ * The ordered sites are split into groups k = 0 .. ceil(D/p) - 1 of p
+ * consecutive sites [k p, min(k p + p, D)); group k is conditioned on a set
+ * C_k of earlier sites (all < k p), and
+ *   log P ~ sum_k [ log Phi(u_{C_k}, u_{G_k}) - log Phi(u_{C_k}) ]
+ * with both CDFs from one Genz run on the block (C_k ascending, G_k): the
+ * conditioning CDF is the leading |C_k|-dim block.  p = 1 with the nearest
+ * neighbours is Eq. vecchia-cdf. */
+typedef enum {
+    VECCHIA_COND_NEAREST = 0, /* union of the m nearest earlier sites of each member (first method) */
+    VECCHIA_COND_RANDOM = 1   /* m sites drawn uniformly without replacement among the earlier ones
+                                 (second method; the third is m = p m') */
+} vecchia_cond_method;
+
+/* Conditioning sets of the groups: cond (ceil(D/p) x cmax int32, rows
+ * ascending, -1 padded) and count (ceil(D/p) int32, may be NULL), both host or
+ * both device.  NEAREST: quantised squared distance, ties to the smaller
+ * index, as vecchia_neighbors (p = 1 gives its rows); VECCHIA_ERR_ARG when a
+ * union has more than cmax sites (cmax >= p m always suffices).  RANDOM: a
+ * uniform subset of min(m, k p) sites before group k by Floyd's algorithm,
+ * draw r of group k the integer floor(w (j + 1) / 2^32), w the first word of
+ * Philox4x32-10 with key (seed lo, seed hi) and counter (k lo, r, 0x52C5,
+ * k hi); m <= cmax.  sites_ordered: D x 2 (same memory kind as cond);
+ * 1 <= p, 0 <= m <= VECCHIA_MAX_M, cmax + p <= VECCHIA_MAX_M + 1. */
+int vecchia_group_conditioning(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, int p, int m,
+                               int method, uint64_t seed, int cmax, int32_t* cond, int32_t* count);
+
+/* The grouped log-CDF: as vecchia_log_cdf with the conditioning rows cond
+ * (ceil(D/p) x cmax, from vecchia_group_conditioning or the caller: rows
+ * ascending, entries < k p, -1 padded after the last).  Terms have up to
+ * cmax + p <= VECCHIA_MAX_M + 1 variables.  On VECCHIA_ERR_NOT_PD or a bad
+ * row, vecchia_last_error_site() gives the group index. */
+int vecchia_grouped_log_cdf(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, int p,
+                            const int32_t* cond, int cmax, vecchia_cov cov, const double* u, int64_t N,
+                            int S, uint64_t seed, int precision, double* log_p, double* std_err);
+
 /* ---- building blocks for schedulers (continuous batching) ----------------
  * The result slot of a problem, in device memory; the layout the library
- * writes.  status is a vecchia_status; bad_site the first failing ordered site
+ * writes.  status is a vecchia_status; bad_site the first failing term (the
+ * ordered site, or the group index of a grouped problem)
  * (INT64_MAX when none). */
 typedef struct {
     double log_p;
@@ -161,9 +208,10 @@ typedef struct {
     int32_t reserved;
 } vecchia_result;
 
-/* A range of sites of one problem: the Genz partial means of sites
- * site_begin .. site_begin + site_count - 1 (all shifts) are written into
- * num/den (D x S, device), failures into *result (device).  All arrays are
+/* A range of terms of one problem (sites, or groups when prob.group > 0):
+ * the Genz partial means of terms site_begin .. site_begin + site_count - 1
+ * (all shifts) are written into num/den (terms x S, device), failures into
+ * *result (device).  All arrays are
  * device memory that stays valid until the work has run on the stream. */
 typedef struct {
     vecchia_problem prob;
@@ -244,11 +292,12 @@ int vecchia_lattice(int64_t N, int dim, uint32_t* g);
 int vecchia_shifts(uint64_t seed, int S, int dim, double* delta);
 
 /* Launch tile of the fused Genz kernel for one precision and block bucket
- * (bucket b holds problems with m + 1 <= 9, 13, 17, 21, 25, 29, 32 for
- * b = 0..6; -1 = all): warps per CTA (1..16), points per lane per pass (1 or
- * 2; FP64 uses 1),
+ * (bucket b holds problems whose largest term has d <= 9, 13, 17, 21, 25,
+ * 29, 32, 48, 64 variables for b = 0..8 -- d = m + 1, or m + p for groups of
+ * p; -1 = all): warps per CTA (1..16; at most 8 above 32 variables), points
+ * per lane per pass (1 or 2; FP64 and blocks above 32 variables use 1),
  * lattice slices per shift spread over a CTA's warps (>= 1), shift groups per
- * site spread over CTAs (1..VECCHIA_MAX_S).  Tiles change only the launch
+ * term spread over CTAs (1..VECCHIA_MAX_S).  Tiles change only the launch
  * shape; results are identical up to the order of the final FP64 sums. */
 int vecchia_set_tile(vecchia_ctx* ctx, int precision, int bucket, int warps, int points,
                      int slices, int groups);

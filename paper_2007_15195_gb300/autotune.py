@@ -17,17 +17,19 @@ import numpy as np
 
 from . import binding as B
 
-# DMAX of each bucket (a problem with m neighbours uses the first DMAX >= m + 1)
-BUCKET_DMAX = (9, 13, 17, 21, 25, 29, 32)
+# DMAX of each bucket (a problem whose largest term has d variables -- m + 1,
+# or m + p for groups of p -- uses the first DMAX >= d)
+BUCKET_DMAX = (9, 13, 17, 21, 25, 29, 32, 48, 64)
 
 DEFAULT_CANDIDATES = [(w, p, 1, g) for w in (2, 4, 8) for p in (1, 2) for g in (1, 2, 4, 8)]
 
 
-def bucket_of(m):
+def bucket_of(m, group=0):
+    need = m + (group if group > 0 else 1)
     for b, d in enumerate(BUCKET_DMAX):
-        if m + 1 <= d:
+        if need <= d:
             return b
-    raise ValueError("m > 31")
+    raise ValueError("terms of more than 64 variables")
 
 
 def default_cache_path():
@@ -44,8 +46,7 @@ def _device_name(device):
 
 
 def _key(ctx, precision, problems):
-    ms = sorted({int(p["m"]) for p in problems})
-    buckets = sorted({bucket_of(m) for m in ms})
+    buckets = sorted({bucket_of(int(p["m"]), int(p.get("group", 0))) for p in problems})
     Ns = sorted({int(p["N"]) for p in problems})
     Ss = sorted({int(p["S"]) for p in problems})
     sites = sum(int(p["sites"].shape[0]) for p in problems)

@@ -24,9 +24,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libvecchia.so")
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_PD, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6, -7)
 ORDER_XY, ORDER_MAXMIN, ORDER_IDENTITY = 0, 1, 2
-COV_EXPONENTIAL, COV_MATERN = 0, 1
+COV_EXPONENTIAL, COV_MATERN, COV_ANISO_EXP = 0, 1, 2
 FP64, MIXED = 0, 1
-MAX_M, MAX_S = 31, 64
+COND_NEAREST, COND_RANDOM = 0, 1
+MAX_M, MAX_S = 63, 64
 ORDER_KINDS = {"xy": ORDER_XY, "maxmin": ORDER_MAXMIN, "identity": ORDER_IDENTITY}
 
 
@@ -42,13 +43,13 @@ class VecchiaError(RuntimeError):
 
 class vecchia_cov(C.Structure):
     _fields_ = [("kind", C.c_int32), ("variance", C.c_double), ("range", C.c_double),
-                ("nu", C.c_double), ("nugget", C.c_double)]
+                ("nu", C.c_double), ("nugget", C.c_double), ("angle", C.c_double), ("aspect", C.c_double)]
 
 
 class vecchia_problem(C.Structure):
     _fields_ = [("sites", C.c_void_p), ("nbr", C.c_void_p), ("u", C.c_void_p), ("D", C.c_int64),
                 ("m", C.c_int32), ("S", C.c_int32), ("N", C.c_int64), ("seed", C.c_uint64),
-                ("cov", vecchia_cov)]
+                ("cov", vecchia_cov), ("group", C.c_int32), ("reserved", C.c_int32)]
 
 
 class vecchia_segment(C.Structure):
@@ -100,6 +101,11 @@ def lib():
         L.vecchia_mixture_log_cdf.argtypes = [_vp, _vp, C.c_int64, _vp, C.c_int, vecchia_cov, _vp,
                                               C.c_int64, C.c_int, C.c_uint64, C.c_double, C.c_double,
                                               C.c_int, C.c_int, C.POINTER(C.c_double),
+                                              C.POINTER(C.c_double)]
+        L.vecchia_group_conditioning.argtypes = [_vp, _vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                                 C.c_int, _vp, _vp]
+        L.vecchia_grouped_log_cdf.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, C.c_int, vecchia_cov, _vp,
+                                              C.c_int64, C.c_int, C.c_uint64, C.c_int, C.POINTER(C.c_double),
                                               C.POINTER(C.c_double)]
         L.vecchia_lattice.argtypes = [C.c_int64, C.c_int, _vp]
         L.vecchia_shifts.argtypes = [C.c_uint64, C.c_int, C.c_int, _vp]
@@ -168,10 +174,15 @@ def _check(st, where, ctx=None):
         raise VecchiaError(st, where, site)
 
 
-def make_cov(kind=COV_EXPONENTIAL, variance=1.0, range_=0.1, nu=0.5, nugget=0.0):
+def make_cov(kind=COV_EXPONENTIAL, variance=1.0, range_=0.1, nu=0.5, nugget=0.0, angle=0.0, aspect=1.0):
+    """A vecchia_cov from arguments or a tuple (kind, variance, range, nu, nugget[, angle, aspect])."""
+    if isinstance(kind, vecchia_cov):
+        return kind
     if isinstance(kind, (tuple, list)):
-        kind, variance, range_, nu, nugget = kind
-    return vecchia_cov(int(kind), float(variance), float(range_), float(nu), float(nugget))
+        t = tuple(kind) + (0.0, 1.0)[len(kind) - 5:] if len(kind) < 7 else tuple(kind)
+        kind, variance, range_, nu, nugget, angle, aspect = t
+    return vecchia_cov(int(kind), float(variance), float(range_), float(nu), float(nugget), float(angle),
+                       float(aspect))
 
 
 # ------------------------------ the context ---------------------------------
@@ -260,6 +271,40 @@ def vecchia_log_cdf(ctx, sites_ordered, nbr, m, cov, u, N, S, seed=0, precision=
     return lp.value, se.value
 
 
+def vecchia_group_conditioning(ctx, sites_ordered, p, m, method=COND_NEAREST, seed=0, cmax=None):
+    """Conditioning rows of the groups of p consecutive ordered sites: returns
+    (cond [ceil(D/p), cmax], count [ceil(D/p)]) on the sites' device (method
+    COND_NEAREST: union of each member's m nearest earlier sites, cmax default
+    p m; COND_RANDOM: m uniform earlier sites, cmax default m)."""
+    s = _f64(sites_ordered)
+    D = s.shape[0]
+    p, m = int(p), int(m)
+    if cmax is None:
+        cmax = p * m if method == COND_NEAREST else m
+    G = (D + p - 1) // p
+    i32 = torch.int32 if torch is not None else None
+    cond = _empty_like_kind(s, (G, max(int(cmax), 1)), np.int32, i32)
+    cnt = _empty_like_kind(s, (G,), np.int32, i32)
+    _check(lib().vecchia_group_conditioning(ctx.handle, _ptr(s), D, p, m, int(method), C.c_uint64(int(seed)),
+                                            int(cmax), _ptr(cond), _ptr(cnt)), "vecchia_group_conditioning",
+           ctx)
+    return cond[:, :int(cmax)], cnt
+
+
+def vecchia_grouped_log_cdf(ctx, sites_ordered, p, cond, cov, u, N, S, seed=0, precision=MIXED):
+    """The joint-group Vecchia log-CDF (groups of p ordered sites, conditioning
+    rows cond [ceil(D/p), cmax]); returns (log_p, std_err)."""
+    s, uu = _f64(sites_ordered), _f64(u)
+    cmax = int(cond.shape[1])
+    cd = _i32(cond) if cmax > 0 else None
+    lp, se = C.c_double(), C.c_double()
+    _check(lib().vecchia_grouped_log_cdf(ctx.handle, _ptr(s), s.shape[0], int(p), _ptr(cd), cmax,
+                                         make_cov(cov), _ptr(uu), int(N), int(S), C.c_uint64(int(seed)),
+                                         int(precision), C.byref(lp), C.byref(se)), "vecchia_grouped_log_cdf",
+           ctx)
+    return lp.value, se.value
+
+
 def vecchia_mixture_log_cdf(ctx, sites_ordered, nbr, m, cov, x, N, S, seed=0, beta=0.5, gamma=1.0,
                             n_nodes=16, precision=MIXED):
     s, xx = _f64(sites_ordered), _f64(x)
@@ -313,7 +358,7 @@ def _problem_array(problems):
         nb = _i32(p["nbr"]) if m > 0 else None
         keep.append((s, uu, nb))
         arr[i] = vecchia_problem(_ptr(s), _ptr(nb), _ptr(uu), s.shape[0], m, int(p["S"]), int(p["N"]),
-                                 int(p.get("seed", 0)), make_cov(p["cov"]))
+                                 int(p.get("seed", 0)), make_cov(p["cov"]), int(p.get("group", 0)), 0)
     return arr, keep
 
 
@@ -388,9 +433,9 @@ def vecchia_result_init(ctx, results, n):
     _check(lib().vecchia_result_init(ctx.handle, _ptr(results), int(n)), "vecchia_result_init", ctx)
 
 
-def make_segment(sites, nbr, u, m, cov, N, S, seed, num, den, result_ptr, site_begin, site_count):
+def make_segment(sites, nbr, u, m, cov, N, S, seed, num, den, result_ptr, site_begin, site_count, group=0):
     prob = vecchia_problem(_ptr(sites), _ptr(nbr) if m > 0 else None, _ptr(u), sites.shape[0], int(m),
-                           int(S), int(N), int(seed), make_cov(cov))
+                           int(S), int(N), int(seed), make_cov(cov), int(group), 0)
     return vecchia_segment(prob, _ptr(num), _ptr(den), result_ptr, int(site_begin), int(site_count))
 
 

@@ -231,13 +231,27 @@ bool cov_ok(const vecchia_cov& c) {
     if (!std::isfinite(c.variance) || !std::isfinite(c.range) || !std::isfinite(c.nugget)) return false;
     if (c.kind == VECCHIA_COV_EXPONENTIAL) return true;
     if (c.kind == VECCHIA_COV_MATERN) return c.nu == 0.5 || c.nu == 1.5 || c.nu == 2.5;
+    if (c.kind == VECCHIA_COV_ANISO_EXP)
+        return std::isfinite(c.angle) && std::isfinite(c.aspect) && c.aspect > 0.0;
     return false;
+}
+
+void set_cov(ProbDev& d, const vecchia_cov& c) {
+    d.variance = c.variance;
+    d.range = c.range;
+    d.nu = c.nu;
+    d.nugget = c.nugget;
+    d.cov_kind = c.kind;
+    d.cos_a = (c.kind == VECCHIA_COV_ANISO_EXP) ? std::cos(c.angle) : 1.0;
+    d.sin_a = (c.kind == VECCHIA_COV_ANISO_EXP) ? std::sin(c.angle) : 0.0;
+    d.aspect = (c.kind == VECCHIA_COV_ANISO_EXP) ? c.aspect : 1.0;
 }
 
 int check_problem(const vecchia_problem& p) {
     if (p.D < 1 || p.D > INT_MAX / 2 || !p.sites || !p.u) return VECCHIA_ERR_ARG;
-    if (p.m < 0) return VECCHIA_ERR_ARG;
-    if (p.m > VECCHIA_MAX_M) return VECCHIA_ERR_UNSUPPORTED;
+    if (p.m < 0 || p.group < 0) return VECCHIA_ERR_ARG;
+    if (p.m > VECCHIA_MAX_M || vk::max_term_dim(p.m, p.group) > VECCHIA_MAX_M + 1)
+        return VECCHIA_ERR_UNSUPPORTED;
     if (p.m > 0 && !p.nbr) return VECCHIA_ERR_ARG;
     if (p.N < 1 || p.N > INT_MAX) return VECCHIA_ERR_ARG;
     if (p.S < 2 || p.S > VECCHIA_MAX_S) return VECCHIA_ERR_ARG;
@@ -269,8 +283,17 @@ uint32_t* lattice_for(vecchia_ctx* c, int64_t N) {
 // (registers allow the second independent chain there), one above; enough
 // shift groups (a power of two, so S = 2^k splits evenly) for ~4096 CTA items,
 // but never fewer shifts per item than warps (a warp without a unit idles).
+// Blocks above 32 variables: 8 warps and every shift in one item, so the
+// one-warp Cholesky of up to 64 variables is shared by the most work.
 GenzTile default_tile(bool mixed, int64_t total_sites, int max_S, int bucket) {
     GenzTile t;
+    if (vk::kDmaxBuckets[bucket] > 32) {
+        t.warps = 8;
+        t.points = 1;
+        t.slices = 1;
+        t.groups = 1;
+        return t;
+    }
     t.warps = 4;
     t.points = (mixed && vk::kDmaxBuckets[bucket] <= 21) ? 2 : 1;
     t.slices = 1;
@@ -295,8 +318,10 @@ struct Batch {
     bool mixed = false, host_in = false, terms_host = false;
     std::vector<vecchia_problem> probs;
     std::vector<int> ok;
-    int64_t total_sites = 0, fb_cap = 0, max_slices = 0;
+    int64_t total_sites = 0, fb_cap = 0, max_slices = 0;  // total_sites: terms of all problems
+    int64_t total_shift_rows = 0;
     int max_S[NB] = {0};
+    int max_S_all = 0, max_bucket = 0;
     int64_t bucket_sites[NB] = {0};
     int bucket_segs[NB] = {0};
     GenzTile tiles[NB];
@@ -344,13 +369,17 @@ int prepare(vecchia_ctx* c, const vecchia_problem* probs, int n, int precision, 
     B.bucket_of.assign(n, -1);
     for (int i = 0; i < n; ++i) {
         if (!B.ok[i]) continue;
-        const int b = vk::bucket_of(probs[i].m + 1);
+        const int b = vk::bucket_of(vk::max_term_dim(probs[i].m, probs[i].group));
+        const int64_t T = vk::n_terms_of(probs[i].D, probs[i].group);
         B.bucket_of[i] = b;
-        B.bucket_sites[b] += probs[i].D;
+        B.bucket_sites[b] += T;
         B.bucket_segs[b] += 1;
         B.max_S[b] = std::max(B.max_S[b], probs[i].S);
-        B.total_sites += probs[i].D;
-        B.max_slices = std::max(B.max_slices, vk::logsum_slices(probs[i].D));
+        B.max_S_all = std::max(B.max_S_all, probs[i].S);
+        B.max_bucket = std::max(B.max_bucket, b);
+        B.total_sites += T;
+        B.total_shift_rows += probs[i].S;
+        B.max_slices = std::max(B.max_slices, vk::logsum_slices(T));
     }
     int max_groups = 1;
     for (int b = 0; b < NB; ++b) {
@@ -376,26 +405,27 @@ int prepare(vecchia_ctx* c, const vecchia_problem* probs, int n, int precision, 
     for (int i = 0; i < n; ++i) {
         if (!B.ok[i]) continue;
         const auto& p = probs[i];
+        const int64_t T = vk::n_terms_of(p.D, p.group);
         if (B.host_in) {
             B.o_sites[i] = dv.off;
             dv.take<double>(2 * p.D);
             B.o_nbr[i] = dv.off;
-            dv.take<int32_t>((size_t)p.D * std::max(p.m, 1));
+            dv.take<int32_t>((size_t)T * std::max(p.m, 1));
             B.o_u[i] = dv.off;
             dv.take<double>(p.D);
         }
         B.o_num[i] = dv.off;
-        dv.take<double>((size_t)p.D * p.S);
+        dv.take<double>((size_t)T * p.S);
         B.o_den[i] = dv.off;
-        dv.take<double>((size_t)p.D * p.S);
-        logsum_doubles += vk::logsum_scratch(p.D, p.S);
+        dv.take<double>((size_t)T * p.S);
+        logsum_doubles += vk::logsum_scratch(T, p.S);
     }
     B.o_means = dv.off;
     dv.take<double>(logsum_doubles);
     B.o_delta = dv.off;
-    dv.take<double>((size_t)n * vk::kMaxS * kDim);
+    dv.take<double>((size_t)B.total_shift_rows * kDim);
     B.o_dfix = dv.off;
-    dv.take<uint32_t>((size_t)n * vk::kMaxS * kDim);
+    dv.take<uint32_t>((size_t)B.total_shift_rows * kDim);
     B.o_fbcount = dv.off;
     dv.take<int>(1);
     B.o_fbitems = dv.off;
@@ -441,17 +471,18 @@ void fill_blob(const Batch& B, char* A, char* H, double* terms) {
     int64_t* hoff = (int64_t*)(H + B.b_off);
     int64_t* hmoff = (int64_t*)(H + B.b_moff);
     double** htp = (double**)(H + B.b_tptr);
-    int64_t moff = 0;
+    int64_t moff = 0, soff = 0;
     for (int i = 0; i < B.n; ++i) {
         const auto& p = B.probs[i];
         ProbDev& d = hp[i];
         std::memset(&d, 0, sizeof(d));
         hseeds[i] = p.seed;
         hS[i] = B.ok[i] ? p.S : 0;
-        hoff[i] = (int64_t)i * vk::kMaxS * kDim;
+        hoff[i] = soff;
         hmoff[i] = moff;
         htp[i] = nullptr;
         if (!B.ok[i]) continue;
+        soff += (int64_t)p.S * kDim;
         d.sites = B.host_in ? (const double*)(A + B.o_sites[i]) : p.sites;
         d.nbr = B.host_in ? (const int32_t*)(A + B.o_nbr[i]) : p.nbr;
         d.u = B.host_in ? (const double*)(A + B.o_u[i]) : p.u;
@@ -462,17 +493,15 @@ void fill_blob(const Batch& B, char* A, char* H, double* terms) {
         d.delta = (const double*)(A + B.o_delta) + hoff[i];
         d.dfix = (const uint32_t*)(A + B.o_dfix) + hoff[i];
         d.D = p.D;
+        d.n_terms = vk::n_terms_of(p.D, p.group);
         d.N = p.N;
-        d.variance = p.cov.variance;
-        d.range = p.cov.range;
-        d.nu = p.cov.nu;
-        d.nugget = p.cov.nugget;
-        d.cov_kind = p.cov.kind;
+        set_cov(d, p.cov);
         d.m = p.m;
+        d.group = p.group;
         d.S = p.S;
         d.dim = kDim;
         if (terms) htp[i] = B.terms_host ? (double*)(A + B.o_terms_out) : terms;
-        moff += vk::logsum_scratch(p.D, p.S);
+        moff += vk::logsum_scratch(d.n_terms, p.S);
     }
     for (int b = 0; b < NB; ++b) {
         int* sp = (int*)(H + B.b_segp[b]);
@@ -482,7 +511,7 @@ void fill_blob(const Batch& B, char* A, char* H, double* terms) {
             if (!B.ok[i] || B.bucket_of[i] != b) continue;
             sp[k] = run;
             sb[k] = make_int2(i, 0);
-            run += (int)B.probs[i].D;
+            run += (int)vk::n_terms_of(B.probs[i].D, B.probs[i].group);
             ++k;
         }
         sp[k] = run;
@@ -497,7 +526,8 @@ cudaError_t stage_inputs(const Batch& B, char* A, cudaStream_t s) {
         const auto& p = B.probs[i];
         e = cudaMemcpyAsync(A + B.o_sites[i], p.sites, sizeof(double) * 2 * p.D, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && p.m > 0)
-            e = cudaMemcpyAsync(A + B.o_nbr[i], p.nbr, sizeof(int32_t) * p.D * p.m, cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(A + B.o_nbr[i], p.nbr, sizeof(int32_t) * vk::n_terms_of(p.D, p.group) * p.m,
+                                cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(A + B.o_u[i], p.u, sizeof(double) * p.D, cudaMemcpyHostToDevice, s);
     }
@@ -525,7 +555,8 @@ cudaError_t enqueue(const Batch& B, char* A, char* H, cudaStream_t s, bool with_
                             res_d, fbc, fbi, B.max_S[b], s);
     }
     if (c && c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
-    if (B.mixed && e == cudaSuccess) e = vk::launch_genz_fallback(probs_d, fbc, fbi, (int)B.fb_cap, res_d, s);
+    if (B.mixed && e == cudaSuccess)
+        e = vk::launch_genz_fallback(B.max_bucket, probs_d, fbc, fbi, (int)B.fb_cap, res_d, B.max_S_all, s);
     if (e == cudaSuccess)
         e = vk::launch_logsum(probs_d, B.n, (int)B.max_slices, res_d,
                               with_terms ? (double* const*)(blob_dev + B.b_tptr) : nullptr,
@@ -581,12 +612,13 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
     if (e == cudaSuccess) e = enqueue(B, A, H, s, terms != nullptr, c);
     if (n == 1 && B.ok[0] && e == cudaSuccess) {
         const auto& p = probs[0];
+        const int64_t T = vk::n_terms_of(p.D, p.group);
         if (B.terms_host)
-            e = cudaMemcpyAsync(terms, A + B.o_terms_out, sizeof(double) * p.D, cudaMemcpyDefault, s);
+            e = cudaMemcpyAsync(terms, A + B.o_terms_out, sizeof(double) * T, cudaMemcpyDefault, s);
         if (num && e == cudaSuccess)
-            e = cudaMemcpyAsync(num, A + B.o_num[0], sizeof(double) * p.D * p.S, cudaMemcpyDefault, s);
+            e = cudaMemcpyAsync(num, A + B.o_num[0], sizeof(double) * T * p.S, cudaMemcpyDefault, s);
         if (den && e == cudaSuccess)
-            e = cudaMemcpyAsync(den, A + B.o_den[0], sizeof(double) * p.D * p.S, cudaMemcpyDefault, s);
+            e = cudaMemcpyAsync(den, A + B.o_den[0], sizeof(double) * T * p.S, cudaMemcpyDefault, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -655,7 +687,7 @@ char* async_stage(vecchia_ctx* c, size_t bytes, int* which) {
 
 bool segment_ok(const vecchia_segment& g) {
     return check_problem(g.prob) == VECCHIA_OK && g.num && g.den && g.result && g.site_begin >= 0 &&
-           g.site_count >= 0 && g.site_begin + g.site_count <= g.prob.D;
+           g.site_count >= 0 && g.site_begin + g.site_count <= vk::n_terms_of(g.prob.D, g.prob.group);
 }
 
 void fill_probdev(ProbDev& d, const vecchia_segment& g, uint32_t* lat, char* A, size_t o_delta,
@@ -672,13 +704,11 @@ void fill_probdev(ProbDev& d, const vecchia_segment& g, uint32_t* lat, char* A, 
     d.delta = (const double*)(A + o_delta) + off;
     d.dfix = (const uint32_t*)(A + o_dfix) + off;
     d.D = p.D;
+    d.n_terms = vk::n_terms_of(p.D, p.group);
     d.N = p.N;
-    d.variance = p.cov.variance;
-    d.range = p.cov.range;
-    d.nu = p.cov.nu;
-    d.nugget = p.cov.nugget;
-    d.cov_kind = p.cov.kind;
+    set_cov(d, p.cov);
     d.m = p.m;
+    d.group = p.group;
     d.S = p.S;
     d.dim = kDim;
     d.res = (ProbResult*)g.result;
@@ -1013,7 +1043,7 @@ int vecchia_log_cdf_terms(vecchia_ctx* c, const double* sites, int64_t D, const 
                           vecchia_cov cov, const double* u, int64_t N, int S, uint64_t seed,
                           int precision, double* log_p, double* std_err, double* terms, double* num,
                           double* den) {
-    vecchia_problem p;
+    vecchia_problem p{};
     p.sites = sites;
     p.nbr = nbr;
     p.u = u;
@@ -1037,6 +1067,103 @@ int vecchia_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, const int32_
     if (!log_p || !std_err) return VECCHIA_ERR_ARG;
     return vecchia_log_cdf_terms(c, sites, D, nbr, m, cov, u, N, S, seed, precision, log_p, std_err,
                                  nullptr, nullptr, nullptr);
+}
+
+int vecchia_grouped_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, int p, const int32_t* cond,
+                            int cmax, vecchia_cov cov, const double* u, int64_t N, int S, uint64_t seed,
+                            int precision, double* log_p, double* std_err) {
+    if (!log_p || !std_err || p < 1) return VECCHIA_ERR_ARG;
+    vecchia_problem pr{};
+    pr.sites = sites;
+    pr.nbr = cond;
+    pr.u = u;
+    pr.D = D;
+    pr.m = cmax;
+    pr.S = S;
+    pr.N = N;
+    pr.seed = seed;
+    pr.cov = cov;
+    pr.group = p;
+    int32_t status = VECCHIA_OK;
+    return run_problems(c, &pr, 1, precision, log_p, std_err, &status, nullptr, nullptr, nullptr);
+}
+
+int vecchia_group_conditioning(vecchia_ctx* c, const double* sites, int64_t D, int p, int m, int method,
+                               uint64_t seed, int cmax, int32_t* cond, int32_t* count) {
+    if (!c || D < 1 || D > INT_MAX / 2 || p < 1 || m < 0 || cmax < 0) return VECCHIA_ERR_ARG;
+    if (method != VECCHIA_COND_NEAREST && method != VECCHIA_COND_RANDOM) return VECCHIA_ERR_ARG;
+    if (m > VECCHIA_MAX_M || cmax + p > VECCHIA_MAX_M + 1) return VECCHIA_ERR_UNSUPPORTED;
+    if (method == VECCHIA_COND_RANDOM && m > cmax) return VECCHIA_ERR_ARG;
+    if (method == VECCHIA_COND_NEAREST && !sites) return VECCHIA_ERR_ARG;
+    const int64_t G = (D + p - 1) / p;
+    if (cmax == 0) {
+        if (count) {
+            if (is_device_ptr(count)) {
+                if (cudaSetDevice(c->device) != cudaSuccess ||
+                    cudaMemsetAsync(count, 0, sizeof(int32_t) * G, c->stream) != cudaSuccess ||
+                    cudaStreamSynchronize(c->stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    return VECCHIA_ERR_CUDA;
+                }
+            } else {
+                std::memset(count, 0, sizeof(int32_t) * G);
+            }
+        }
+        return VECCHIA_OK;
+    }
+    if (!cond) return VECCHIA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    const bool dev_out = is_device_ptr(cond);
+    const bool dev_in = method == VECCHIA_COND_NEAREST && is_device_ptr(sites);
+    if (count && is_device_ptr(count) != dev_out) return VECCHIA_ERR_ARG;
+    const int mm = std::max(m, 1);
+    Carve dv(nullptr);
+    const size_t o_s = dv.off;
+    if (method == VECCHIA_COND_NEAREST && !dev_in) dv.take<double>(2 * D);
+    const size_t o_per = dv.off;
+    if (method == VECCHIA_COND_NEAREST) dv.take<int32_t>((size_t)D * mm);
+    const size_t o_cond = dv.off;
+    if (!dev_out) dv.take<int32_t>((size_t)G * cmax);
+    const size_t o_cnt = dv.off;
+    dv.take<int32_t>((size_t)G);
+    const size_t o_over = dv.off;
+    dv.take<int>(1);
+    const size_t o_scr = dv.off;
+    if (method == VECCHIA_COND_NEAREST) dv.take<char>(vk::knn_scratch_bytes(D));
+    int st = ensure_arena(c, dv.off);
+    if (st != VECCHIA_OK) return st;
+    char* A = (char*)c->arena;
+    const cudaStream_t s = c->stream;
+    int32_t* cd = dev_out ? cond : (int32_t*)(A + o_cond);
+    int32_t* cnt = (count && dev_out) ? count : (int32_t*)(A + o_cnt);
+    int* over = (int*)(A + o_over);
+    cudaError_t e = cudaMemsetAsync(over, 0, sizeof(int), s);
+    if (method == VECCHIA_COND_NEAREST) {
+        const double* sd = dev_in ? sites : (const double*)(A + o_s);
+        int32_t* per = (int32_t*)(A + o_per);
+        if (e == cudaSuccess && !dev_in)
+            e = cudaMemcpyAsync(A + o_s, sites, sizeof(double) * 2 * D, cudaMemcpyHostToDevice, s);
+        if (m > 0) {
+            if (e == cudaSuccess) e = vk::launch_knn(sd, D, m, per, A + o_scr, s, p);
+        } else if (e == cudaSuccess) {
+            e = cudaMemsetAsync(per, 0xff, sizeof(int32_t) * D, s);  // m = 0: one empty row per site
+        }
+        if (e == cudaSuccess) e = vk::launch_group_union(per, D, mm, p, cmax, cd, cnt, over, s);
+    } else if (e == cudaSuccess) {
+        e = vk::launch_group_random(D, p, m, seed, cmax, cd, cnt, s);
+    }
+    int h_over = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_over, over, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !dev_out)
+        e = cudaMemcpyAsync(cond, cd, sizeof(int32_t) * G * cmax, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && count && !dev_out)
+        e = cudaMemcpyAsync(count, cnt, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    return h_over ? VECCHIA_ERR_ARG : VECCHIA_OK;
 }
 
 int vecchia_mixture_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, const int32_t* nbr, int m,
@@ -1118,13 +1245,16 @@ int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, i
         if (!segment_ok(segs[i])) return VECCHIA_ERR_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
     const bool mixed = precision == VECCHIA_MIXED;
-    int64_t bucket_sites[NB] = {0}, total_sites = 0;
-    int bucket_segs[NB] = {0}, max_S[NB] = {0};
+    int64_t bucket_sites[NB] = {0}, total_sites = 0, shift_rows = 0;
+    int bucket_segs[NB] = {0}, max_S[NB] = {0}, max_S_all = 0, max_bucket = 0;
     std::vector<int> bk(n);
     std::vector<uint32_t*> lat(n);
     for (int i = 0; i < n; ++i) {
         const auto& p = segs[i].prob;
-        bk[i] = vk::bucket_of(p.m + 1);
+        bk[i] = vk::bucket_of(vk::max_term_dim(p.m, p.group));
+        max_S_all = std::max(max_S_all, p.S);
+        max_bucket = std::max(max_bucket, bk[i]);
+        shift_rows += p.S;
         bucket_sites[bk[i]] += segs[i].site_count;
         bucket_segs[bk[i]] += segs[i].site_count > 0;
         max_S[bk[i]] = std::max(max_S[bk[i]], p.S);
@@ -1142,9 +1272,9 @@ int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, i
     const int64_t fb_cap = mixed ? std::max<int64_t>(total_sites * max_groups, 1) : 1;
     Carve dv(nullptr);
     const size_t o_delta = dv.off;
-    dv.take<double>((size_t)n * vk::kMaxS * kDim);
+    dv.take<double>((size_t)shift_rows * kDim);
     const size_t o_dfix = dv.off;
-    dv.take<uint32_t>((size_t)n * vk::kMaxS * kDim);
+    dv.take<uint32_t>((size_t)shift_rows * kDim);
     const size_t o_fbc = dv.off;
     dv.take<int>(1);
     const size_t o_fbi = dv.off;
@@ -1175,8 +1305,7 @@ int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, i
     if (!H) return VECCHIA_ERR_NOMEM;
     char* A = (char*)c->arena;
     ProbDev* hp = (ProbDev*)(H + b_probs);
-    for (int i = 0; i < n; ++i) {
-        const int64_t off = (int64_t)i * vk::kMaxS * kDim;
+    for (int i = 0, off = 0; i < n; off += segs[i].prob.S * kDim, ++i) {
         fill_probdev(hp[i], segs[i], lat[i], A, o_delta, o_dfix, off);
         ((uint64_t*)(H + b_seeds))[i] = segs[i].prob.seed;
         ((int32_t*)(H + b_S))[i] = segs[i].prob.S;
@@ -1213,7 +1342,7 @@ int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, i
                             fbc, (int2*)(A + o_fbi), max_S[b], s);
     }
     if (mixed && e == cudaSuccess)
-        e = vk::launch_genz_fallback(probs_d, fbc, (int2*)(A + o_fbi), (int)fb_cap, nullptr, s);
+        e = vk::launch_genz_fallback(max_bucket, probs_d, fbc, (int2*)(A + o_fbi), (int)fb_cap, nullptr, max_S_all, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return VECCHIA_ERR_CUDA;
@@ -1229,8 +1358,9 @@ int vecchia_reduce_async(vecchia_ctx* c, const vecchia_segment* probs, int n) {
     if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
     int64_t scratch = 0, max_slices = 0;
     for (int i = 0; i < n; ++i) {
-        scratch += vk::logsum_scratch(probs[i].prob.D, probs[i].prob.S);
-        max_slices = std::max(max_slices, vk::logsum_slices(probs[i].prob.D));
+        const int64_t T = vk::n_terms_of(probs[i].prob.D, probs[i].prob.group);
+        scratch += vk::logsum_scratch(T, probs[i].prob.S);
+        max_slices = std::max(max_slices, vk::logsum_slices(T));
     }
     Carve dv(nullptr);
     const size_t o_scr = dv.off;
@@ -1253,7 +1383,7 @@ int vecchia_reduce_async(vecchia_ctx* c, const vecchia_segment* probs, int n) {
     for (int i = 0; i < n; ++i) {
         fill_probdev(((ProbDev*)(H + b_probs))[i], probs[i], nullptr, A, 0, 0, 0);
         ((int64_t*)(H + b_off))[i] = run;
-        run += vk::logsum_scratch(probs[i].prob.D, probs[i].prob.S);
+        run += vk::logsum_scratch(vk::n_terms_of(probs[i].prob.D, probs[i].prob.group), probs[i].prob.S);
     }
     const cudaStream_t s = c->stream;
     char* blob = A + o_blob;
@@ -1327,13 +1457,7 @@ int vecchia_plan_run(vecchia_plan* P, const uint64_t* seeds, const vecchia_cov* 
     uint64_t* hseeds = (uint64_t*)(P->H + B.b_seeds);
     for (int i = 0; i < B.n; ++i) {
         if (seeds) hseeds[i] = seeds[i];
-        if (covs && B.ok[i]) {
-            hp[i].variance = covs[i].variance;
-            hp[i].range = covs[i].range;
-            hp[i].nu = covs[i].nu;
-            hp[i].nugget = covs[i].nugget;
-            hp[i].cov_kind = covs[i].kind;
-        }
+        if (covs && B.ok[i]) set_cov(hp[i], covs[i]);
         status[i] = B.ok[i] ? VECCHIA_OK : VECCHIA_ERR_ARG;
     }
     cudaError_t e = cudaEventRecord(P->ready, P->c->stream);

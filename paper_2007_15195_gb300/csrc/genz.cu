@@ -20,8 +20,17 @@
 // The partial sums u_v - sum_j L_vj y_j of all later variables are kept in
 // registers and updated right after each y_t (right-looking), so the loop over
 // t runs at run time with a fixed register array per lane.
+//
+// A term is a block of d variables whose first c are the conditioning set:
+// one site i with c = |N_i| (Eq. vecchia-cdf), or a group of p sites with
+// its conditioning set (Sec. 3.2).  Its denominator is the c-dim CDF of the
+// leading block, i.e. the product e_0 ... e_{c-1} of the same run (1 when
+// c = 0); the numerator is the full product.
 #include <cfloat>
 #include <climits>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "special_f32.h"
 #include "vk_internal.h"
@@ -32,8 +41,19 @@ namespace {
 constexpr int kMaxWarps = 16;
 constexpr int kMaxUnits = 64;  // shifts x slices handled by one CTA item
 
+// Distance between two sites: Euclidean, or the Mahalanobis distance of
+// Sec. 4.1 for the anisotropic exponential (explicit roundings, no contraction).
+__device__ __forceinline__ double site_dist(const ProbDev& P, double dx, double dy) {
+    if (P.cov_kind == VECCHIA_COV_ANISO_EXP) {
+        const double o1 = __dsub_rn(__dmul_rn(dx, P.cos_a), __dmul_rn(dy, P.sin_a));
+        const double o2 = __dmul_rn(P.aspect, __dadd_rn(__dmul_rn(dx, P.sin_a), __dmul_rn(dy, P.cos_a)));
+        return sqrt(__dadd_rn(__dmul_rn(o1, o1), __dmul_rn(o2, o2)));
+    }
+    return sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+}
+
 __device__ __forceinline__ double cov_fn(int kind, double var, double range, double nu, double h) {
-    if (kind == VECCHIA_COV_EXPONENTIAL || nu == 0.5) return var * exp(-h / range);
+    if (kind != VECCHIA_COV_MATERN || nu == 0.5) return var * exp(-h / range);
     if (nu == 1.5) {
         const double a = 1.7320508075688772935 * h / range;
         return var * (1.0 + a) * exp(-a);
@@ -42,12 +62,16 @@ __device__ __forceinline__ double cov_fn(int kind, double var, double range, dou
     return var * (1.0 + a + a * a / 3.0) * exp(-a);
 }
 
+// Shared memory of a CTA: this fixed part, then (mixed path) the dynamic
+// tail dfix[S][DMAX] (the shifts in 32-bit fixed point) and
+// stepw[warps][DMAX] (per warp, the step constants of its current shift).
 template <int DMAX, bool MIXED>
 struct GenzSmem {
     using T = typename std::conditional<MIXED, float, double>::type;
     double A[DMAX][DMAX + 1];  // covariance block, overwritten by its Cholesky factor
     double bx[DMAX], by[DMAX], bu[DMAX];
     double diag[DMAX];
+    int bidx[DMAX];            // the block's ordered sites
     // Recursion tables, step t (lattice coordinate t, variable t + 1 next):
     //   Lz[t]      = L_{t+1,t}          coefficient of y_t in variable t+1
     //   Lup[t][r]  = L_{t+2+r,t}        coefficients of y_t in the later variables
@@ -59,15 +83,34 @@ struct GenzSmem {
     __align__(16) T Lz[DMAX];
     __align__(16) T up[DMAX];  // MIXED: u_v / L_vv;  FP64: u_v
     uint32_t gl[DMAX];         // FP64: g_t;  MIXED: round(g_t 2^32 / N)
-    uint32_t dfix[MIXED ? kMaxS : 1][DMAX];
-    // per warp, the step constants of the shift it is working on:
-    // {L_{t+1,t}/L_{t+1,t+1}, round(g_t 2^32/N), shift_t 2^32, 0}, one 16-byte load per step
-    __align__(16) float4 stepw[MIXED ? kMaxWarps : 1][MIXED ? DMAX : 1];
     double part_num[kMaxUnits], part_den[kMaxUnits];
     double e0, ec0;
     float le2_0;  // log2 e0 when e0 < 2^-64 (mixed path)
-    int q, bad, flag;
+    int q, c, bad, flag;
 };
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Bytes of shared memory for a CTA of `warps` warps on problems with <= max_S shifts.
+template <int DMAX, bool MIXED>
+constexpr size_t smem_bytes(int max_S, int warps) {
+    return align16(sizeof(GenzSmem<DMAX, MIXED>)) +
+           (MIXED ? align16((size_t)max_S * DMAX * 4) + (size_t)warps * DMAX * 16 : 0);
+}
+
+extern __shared__ __align__(16) unsigned char vk_smem[];
+
+// The dynamic tail: dfix row of shift s, and the step constants of a warp:
+// {L_{t+1,t}/L_{t+1,t+1}, round(g_t 2^32/N), shift_t 2^32, 0}, one 16-byte load per step.
+template <int DMAX>
+__device__ __forceinline__ uint32_t* dfix_row(int s) {
+    return (uint32_t*)(vk_smem + align16(sizeof(GenzSmem<DMAX, true>))) + s * DMAX;
+}
+template <int DMAX>
+__device__ __forceinline__ float4* stepw_of(int max_S, int warp) {
+    return (float4*)(vk_smem + align16(sizeof(GenzSmem<DMAX, true>)) + align16((size_t)max_S * DMAX * 4)) +
+           warp * DMAX;
+}
 
 // Phi(z) and 1 - Phi(z), the smaller one from the tail to full precision.
 __device__ __forceinline__ void phi_pair64(double z, double& e, double& ec) {
@@ -157,22 +200,25 @@ __device__ __forceinline__ void mixed_steps(const GenzSmem<DMAX, true>& sm, cons
     }
 }
 
+// Steps t <= t' < t_stop of a term with q steps, in phases of update width
+// W, W - 8, ...: a step needs width q - t' - 1.
 template <int DMAX, int P, int W>
 __device__ __forceinline__ void mixed_phases(const GenzSmem<DMAX, true>& sm, const uint32_t* dfs,
-                                             int t, int q, MixedLanes<DMAX, P>& L) {
+                                             int t, int t_stop, int q, MixedLanes<DMAX, P>& L) {
     constexpr int WN = W - 8;
-    const int t_end = (WN > 0) ? max(t, min(q, q - 1 - WN)) : q;
+    const int t_end = (WN > 0) ? max(t, min(t_stop, q - 1 - WN)) : t_stop;
     mixed_steps<DMAX, P, W>(sm, dfs, t, t_end, L);
-    if constexpr (WN > 0) mixed_phases<DMAX, P, WN>(sm, dfs, t_end, q, L);
+    if constexpr (WN > 0) mixed_phases<DMAX, P, WN>(sm, dfs, t_end, t_stop, q, L);
 }
 
 template <int DMAX, int P>
-__device__ __forceinline__ void genz_points_safe(const GenzSmem<DMAX, true>& sm, int q, int s,
+__device__ __forceinline__ void genz_points_safe(const GenzSmem<DMAX, true>& sm, int q, int c, int s,
                                                   int64_t k_begin, int64_t k_end, double& acc_num,
                                                   double& acc_den) {
     constexpr int W0 = (DMAX - 2 > 0) ? DMAX - 2 : 1;
     const int lane = threadIdx.x & 31;
-    const uint32_t* dfs = sm.dfix[s];
+    const uint32_t* dfs = dfix_row<DMAX>(s);
+    const int cut = (c >= 1) ? c : q;  // after steps 0 .. cut-1, g = e_1 ... e_{c-1}
     const float e0f = (float)sm.e0, ec0f = (float)sm.ec0;
     const bool tiny0 = sm.e0 < 0x1p-64;
     for (int64_t kb = k_begin; kb < k_end; kb += 32 * P) {
@@ -192,11 +238,15 @@ __device__ __forceinline__ void genz_points_safe(const GenzSmem<DMAX, true>& sm,
             L.g[p] = 1.0f;
             L.E[p] = 0;
         }
-        mixed_phases<DMAX, P, W0>(sm, dfs, 0, q, L);
+        mixed_phases<DMAX, P, W0>(sm, dfs, 0, cut, q, L);
+        double den_c[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) den_c[p] = (double)L.g[p] * pow2_neg(L.E[p]);
+        mixed_phases<DMAX, P, W0>(sm, dfs, cut, q, q, L);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (valid[p]) {
-                const double den = (double)L.g[p] * pow2_neg(L.E[p]);
+                const double den = den_c[p];
                 float gn = L.g[p];
                 int En = L.E[p];
                 if (!L.tiny[p])
@@ -252,33 +302,45 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
     }
 }
 
-// Steps t0 <= t < q (t0 >= 1) in phases of update width W, W - 4, ...: a step
-// needs width q - t - 1, so the phase of width W ends where W - 4 suffices.
-template <int DMAX, int P, int W>
+// Steps t <= t' < q (t >= 1) of a term with q steps, in phases of update width
+// W, W - 4, ...: a step needs width q - t' - 1, so the phase of width W ends
+// where W - 4 suffices.  CAPTURE (terms whose conditioning set is shorter
+// than q): at the start of step c (warp-uniform), gd = g = e_1 ... e_{c-1},
+// the conditioning CDF's sample.  A classic term (c = q) uses g at the end
+// and runs the instantiation without the check.
+template <int DMAX, int P, int W, bool CAPTURE>
 __device__ __forceinline__ void fast_phases(const GenzSmem<DMAX, true>& sm, const float4* sc, int t,
-                                            int q, float (&R)[P][DMAX - 1], float (&e)[P],
-                                            float (&ec)[P], float (&g)[P], const uint32_t (&kk)[P]) {
+                                            int q, int cut, float (&R)[P][DMAX - 1], float (&e)[P],
+                                            float (&ec)[P], float (&g)[P], float (&gd)[P],
+                                            const uint32_t (&kk)[P]) {
     constexpr int WN = W - 4;
     const int t_end = (WN > 0) ? max(t, min(q, q - 1 - WN)) : q;
-    for (int tt = t; tt < t_end; ++tt) fast_step<DMAX, P, W, false>(sm, sc, tt, R, e, ec, g, kk);
-    if constexpr (WN > 0) fast_phases<DMAX, P, WN>(sm, sc, t_end, q, R, e, ec, g, kk);
+    for (int tt = t; tt < t_end; ++tt) {
+        if (CAPTURE && tt == cut) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) gd[p] = g[p];
+        }
+        fast_step<DMAX, P, W, false>(sm, sc, tt, R, e, ec, g, kk);
+    }
+    if constexpr (WN > 0) fast_phases<DMAX, P, WN, CAPTURE>(sm, sc, t_end, q, cut, R, e, ec, g, gd, kk);
 }
 
-template <int DMAX, int P>
-__device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm, int q, int s,
-                                                 int64_t k_begin, int64_t k_end, double& acc_num,
-                                                 double& acc_den) {
+template <int DMAX, int P, bool CAPTURE>
+__device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm, int q, int c, int s,
+                                                 int max_S, int64_t k_begin, int64_t k_end,
+                                                 double& acc_num, double& acc_den) {
     constexpr int W0 = (DMAX - 2 > 0) ? DMAX - 2 : 1;
     const int lane = threadIdx.x & 31;
-    float4* sc = const_cast<float4*>(sm.stepw[threadIdx.x >> 5]);
+    float4* sc = stepw_of<DMAX>(max_S, threadIdx.x >> 5);
+    const uint32_t* dfs = dfix_row<DMAX>(s);
     __syncwarp();
-    if (lane < q) sc[lane] = make_float4(sm.Lz[lane], __uint_as_float(sm.gl[lane]),
-                                         __uint_as_float(sm.dfix[s][lane]), 0.0f);
+    for (int t = lane; t < q; t += 32)
+        sc[t] = make_float4(sm.Lz[t], __uint_as_float(sm.gl[t]), __uint_as_float(dfs[t]), 0.0f);
     __syncwarp();
     const float e0f = (float)sm.e0, ec0f = (float)sm.ec0;
     Kahan32 kn, kd;
     for (int64_t kb = k_begin; kb < k_end; kb += 32 * P) {
-        float R[P][DMAX - 1], e[P], ec[P], g[P];
+        float R[P][DMAX - 1], e[P], ec[P], g[P], gd[P];
         uint32_t kk[P];
         bool valid[P];
 #pragma unroll
@@ -291,13 +353,14 @@ __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm,
             e[p] = e0f;
             ec[p] = ec0f;
             g[p] = 1.0f;
+            gd[p] = 1.0f;  // c = 1: e_0 alone (factored out)
         }
         fast_step<DMAX, P, W0, true>(sm, sc, 0, R, e, ec, g, kk);  // q >= 1: step 0 at full width
-        fast_phases<DMAX, P, W0>(sm, sc, 1, q, R, e, ec, g, kk);
+        fast_phases<DMAX, P, W0, CAPTURE>(sm, sc, 1, q, c, R, e, ec, g, gd, kk);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (valid[p]) {
-                kd.add(g[p]);
+                kd.add(CAPTURE ? gd[p] : g[p]);
                 kn.add(__fmul_rn(g[p], e[p]));
             }
         }
@@ -310,7 +373,7 @@ __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm,
 
 template <int DMAX>
 __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm, const ProbDev& P,
-                                                 int q, int s, int64_t k_begin, int64_t k_end,
+                                                 int q, int c, int s, int64_t k_begin, int64_t k_end,
                                                  double& acc_num, double& acc_den) {
     constexpr int W = DMAX - 2;
     const int lane = threadIdx.x & 31;
@@ -321,9 +384,10 @@ __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm
         double R[DMAX - 1];
 #pragma unroll
         for (int r = 0; r < DMAX - 1; ++r) R[r] = sm.up[1 + r];
-        double e = sm.e0, ec = sm.ec0, f = 1.0;
+        double e = sm.e0, ec = sm.ec0, f = 1.0, fc = 1.0;
         for (int t = 0; t < q; ++t) {
             f *= e;  // e_0 ... e_t
+            if (t + 1 == c) fc = f;  // the c-dim CDF sample of the leading block
             const uint64_t rr = ((uint64_t)k * (uint64_t)sm.gl[t]) % N;
             double x = __dadd_rn((double)rr / Nd, dl[t]);
             if (x >= 1.0) x -= 1.0;
@@ -338,7 +402,7 @@ __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm
             for (int r = 0; r < W; ++r) R[r] = fma(-lup[r], y, R[r + 1]);
             phi_pair64(acc / sm.diag[t + 1], e, ec);
         }
-        acc_den += f;
+        acc_den += fc;
         acc_num += f * e;
     }
 }
@@ -389,6 +453,9 @@ constexpr int kModeFP64 = 0, kModeFast = 1, kModeSafe = 2;
 
 // Register cap per thread: the fast mixed loop keeps DMAX - 1 partial sums per
 // point in registers; capping the rest raises the number of resident warps.
+// Blocks above 32 variables run one point per lane with up to 128 registers
+// (fast) or 255 (FP64 and log-space forms, whose partial sums are wider), and
+// at most 256 threads per CTA.
 #ifndef VK_CAP_P1_SMALL
 #define VK_CAP_P1_SMALL 64
 #endif
@@ -402,19 +469,66 @@ constexpr int kModeFP64 = 0, kModeFast = 1, kModeSafe = 2;
 #define VK_CAP_P2_LARGE 128
 #endif
 __host__ __device__ constexpr int reg_cap(int dmax, int p, int mode) {
-    return mode != kModeFast ? 128
-           : p == 1        ? (dmax <= 16 ? VK_CAP_P1_SMALL : VK_CAP_P1_LARGE)
-                           : (dmax <= 16 ? VK_CAP_P2_SMALL : VK_CAP_P2_LARGE);
+    return dmax > 32            ? (mode == kModeFast ? 128 : 255)
+           : mode != kModeFast ? 128
+           : p == 1            ? (dmax <= 16 ? VK_CAP_P1_SMALL : VK_CAP_P1_LARGE)
+                               : (dmax <= 16 ? VK_CAP_P2_SMALL : VK_CAP_P2_LARGE);
+}
+__host__ __device__ constexpr int max_threads(int dmax, int p, int mode) {
+    return reg_cap(dmax, p, mode) > 128 ? 256 : 512;
+}
+
+// A term of a problem: its block (the conditioning sites ascending, then the
+// sites of the term) into sm.bidx, c and d; false if the row is malformed.
+// Classic (group 0): term i is site i with N_i = the first min(m, i) entries
+// of row i.  Group p: term k is sites k p .. min(k p + p, D) - 1 with the
+// leading non-negative entries of row k (the rest must be -1).
+template <int DMAX, bool MIXED>
+__device__ __forceinline__ bool term_block(GenzSmem<DMAX, MIXED>& sm, const ProbDev& Pd, int64_t term,
+                                           int& c, int& d, int64_t& i0) {
+    const int lane = threadIdx.x & 31;
+    const int m = Pd.m;
+    const int32_t* row = Pd.nbr + term * (int64_t)m;
+    int g;
+    bool ok = true;
+    if (Pd.group == 0) {
+        i0 = term;
+        g = 1;
+        c = (int)((term < m) ? term : m);
+    } else {
+        i0 = term * Pd.group;
+        g = (int)min((int64_t)Pd.group, Pd.D - i0);
+        c = m;
+        for (int base = 0; base < m; base += 32) {  // first negative entry
+            const int r = base + lane;
+            const unsigned neg = __ballot_sync(0xffffffffu, r < m && row[r] < 0);
+            if (neg) {
+                c = base + __ffs(neg) - 1;
+                break;
+            }
+        }
+        for (int r = c + lane; r < m; r += 32) ok = ok && row[r] < 0;
+    }
+    d = c + g;
+    if (d > DMAX) ok = false;
+    if (ok)
+        for (int v = lane; v < d; v += 32) sm.bidx[v] = (v < c) ? row[v] : (int)(i0 + (v - c));
+    __syncwarp();
+    if (ok)
+        for (int v = lane; v < c; v += 32) {
+            const int idx = sm.bidx[v];
+            ok = ok && idx >= 0 && idx < i0 && (v == 0 || idx > sm.bidx[v - 1]);  // ascending (block order)
+        }
+    return __all_sync(0xffffffffu, ok);
 }
 
 template <int DMAX, int P, int MODE>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(DMAX, P, MODE))
-    genz_kernel(const ProbDev* __restrict__ probs, ItemSrc src,
-                                                   int slices, ProbResult* __restrict__ results,
-                                                   int* __restrict__ fallback_count,
-                                                   int2* __restrict__ fallback_items) {
+__global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_cap(DMAX, P, MODE))
+    genz_kernel(const ProbDev* __restrict__ probs, ItemSrc src, int slices, int max_S,
+                ProbResult* __restrict__ results, int* __restrict__ fallback_count,
+                int2* __restrict__ fallback_items) {
     constexpr bool MIXED = MODE != kModeFP64;
-    __shared__ GenzSmem<DMAX, MIXED> sm;
+    GenzSmem<DMAX, MIXED>& sm = *reinterpret_cast<GenzSmem<DMAX, MIXED>*>(vk_smem);
     using T = typename GenzSmem<DMAX, MIXED>::T;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -426,68 +540,60 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(DMAX, P, MODE))
         int grp;
         item_of(src, it, item, grp);
         const ProbDev& Pd = probs[item.x];
-        const int64_t site = item.y;
-        const int m = Pd.m;
-        const int q = (int)((site < m) ? site : m);
-        const int d = q + 1;
+        const int64_t term = item.y;
         const int S = Pd.S;
         const int groups = src.items ? 1 : src.groups;
         const int s_lo = (S * grp) / groups, s_hi = (S * (grp + 1)) / groups;
 
         // ---- prologue: block, covariance, Cholesky (warp 0, FP64) ----
         if (warp == 0) {
-            int idx = -1;
-            bool ok = true;
-            if (lane < d) {
-                idx = (lane < q) ? Pd.nbr[site * m + lane] : (int)site;
-                if (lane < q) ok = (idx >= 0) && (idx < site);
-            }
-            const int prev = __shfl_up_sync(0xffffffffu, idx, 1);
-            if (lane > 0 && lane < q && idx <= prev) ok = false;  // ascending (Sec. 2.2 block order)
-            const bool all_ok = __all_sync(0xffffffffu, ok);
-            if (all_ok && lane < d) {
-                sm.bx[lane] = Pd.sites[2 * (int64_t)idx];
-                sm.by[lane] = Pd.sites[2 * (int64_t)idx + 1];
-                sm.bu[lane] = Pd.u[idx];
-            }
-            __syncwarp();
-            int bad = all_ok ? 0 : 2;
-            if (!bad && lane < d) {
-                for (int c = 0; c <= lane; ++c) {
-                    const double dx = __dsub_rn(sm.bx[lane], sm.bx[c]);
-                    const double dy = __dsub_rn(sm.by[lane], sm.by[c]);
-                    const double h = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-                    double v = cov_fn(Pd.cov_kind, Pd.variance, Pd.range, Pd.nu, h);
-                    if (c == lane) v += Pd.nugget;
-                    sm.A[lane][c] = v;
+            int c = 0, d = 1;
+            int64_t i0 = 0;
+            int bad = term_block<DMAX, MIXED>(sm, Pd, term, c, d, i0) ? 0 : 2;
+            if (!bad)
+                for (int v = lane; v < d; v += 32) {
+                    const int idx = sm.bidx[v];
+                    sm.bx[v] = Pd.sites[2 * (int64_t)idx];
+                    sm.by[v] = Pd.sites[2 * (int64_t)idx + 1];
+                    sm.bu[v] = Pd.u[idx];
                 }
-            }
             __syncwarp();
-            // Cholesky, column by column; every entry's inner sum runs in
-            // ascending k with fma, as in the row-by-row definition.
+            if (!bad)
+                for (int r = lane; r < d; r += 32)
+                    for (int col = 0; col <= r; ++col) {
+                        const double h = site_dist(Pd, __dsub_rn(sm.bx[r], sm.bx[col]), __dsub_rn(sm.by[r], sm.by[col]));
+                        double v = cov_fn(Pd.cov_kind, Pd.variance, Pd.range, Pd.nu, h);
+                        if (col == r) v += Pd.nugget;
+                        sm.A[r][col] = v;
+                    }
+            __syncwarp();
+            // Cholesky, column by column, lanes over rows; every entry's inner
+            // sum runs in ascending k with fma, as in the row-by-row definition.
             for (int j = 0; j < d && !bad; ++j) {
                 bool piv_ok = true;
-                if (lane == j) {
+                if (lane == (j & 31)) {
                     double s = sm.A[j][j];
                     for (int k = 0; k < j; ++k) s = fma(-sm.A[j][k], sm.A[j][k], s);
                     piv_ok = s > 0.0;
                     sm.A[j][j] = sqrt(s);
                 }
-                if (!__shfl_sync(0xffffffffu, (int)piv_ok, j)) {
+                if (!__shfl_sync(0xffffffffu, (int)piv_ok, j & 31)) {
                     bad = 1;
                     break;
                 }
                 __syncwarp();
-                if (lane > j && lane < d) {
-                    double s = sm.A[lane][j];
-                    for (int k = 0; k < j; ++k) s = fma(-sm.A[lane][k], sm.A[j][k], s);
-                    sm.A[lane][j] = s / sm.A[j][j];
-                }
+                for (int r = lane; r < d; r += 32)
+                    if (r > j) {
+                        double s = sm.A[r][j];
+                        for (int k = 0; k < j; ++k) s = fma(-sm.A[r][k], sm.A[j][k], s);
+                        sm.A[r][j] = s / sm.A[j][j];
+                    }
                 __syncwarp();
             }
             if (lane == 0) {
                 sm.bad = bad;
-                sm.q = q;
+                sm.q = d - 1;
+                sm.c = c;
                 sm.flag = 0;
                 if (!bad) {
                     const double z0 = sm.bu[0] / sm.A[0][0];
@@ -497,10 +603,12 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(DMAX, P, MODE))
             }
         }
         __syncthreads();
+        const int q = sm.q, c = sm.c;
 
         if (!sm.bad) {
             // ---- derived tables for the recursion ----
             constexpr int LS = GenzSmem<DMAX, MIXED>::LS;
+            const int d = q + 1;
             for (int x = threadIdx.x; x < DMAX * LS; x += blockDim.x) {
                 const int t = x / LS, r = x % LS, v = t + 2 + r;
                 T val = (T)0;
@@ -534,7 +642,7 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(DMAX, P, MODE))
             if constexpr (MIXED) {
                 for (int x = threadIdx.x; x < S * DMAX; x += blockDim.x) {
                     const int s = x / DMAX, t = x % DMAX;
-                    sm.dfix[s][t] = (t < q) ? Pd.dfix[(int64_t)s * Pd.dim + t] : 0u;
+                    dfix_row<DMAX>(s)[t] = (t < q) ? Pd.dfix[(int64_t)s * Pd.dim + t] : 0u;
                 }
             }
         }
@@ -547,12 +655,16 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(DMAX, P, MODE))
                 const int s = s_lo + un / slices, h = un % slices;
                 const int64_t k0 = (Pd.N * h) / slices, k1 = (Pd.N * (h + 1)) / slices;
                 double an = 0.0, ad = 0.0;
-                if constexpr (MODE == kModeFast)
-                    genz_points_fast<DMAX, P>(sm, q, s, k0, k1, an, ad);
+                if constexpr (MODE == kModeFast) {
+                    if (c == q)  // classic term (or a group of one): no capture in the loop
+                        genz_points_fast<DMAX, P, false>(sm, q, c, s, max_S, k0, k1, an, ad);
+                    else
+                        genz_points_fast<DMAX, P, true>(sm, q, c, s, max_S, k0, k1, an, ad);
+                }
                 else if constexpr (MODE == kModeSafe)
-                    genz_points_safe<DMAX, P>(sm, q, s, k0, k1, an, ad);
+                    genz_points_safe<DMAX, P>(sm, q, c, s, k0, k1, an, ad);
                 else
-                    genz_points_fp64<DMAX>(sm, Pd, q, s, k0, k1, an, ad);
+                    genz_points_fp64<DMAX>(sm, Pd, q, c, s, k0, k1, an, ad);
                 an = warp_sum(an);
                 ad = warp_sum(ad);
                 if (lane == 0) {
@@ -583,19 +695,22 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(DMAX, P, MODE))
                 if constexpr (MIXED) {
                     vn *= sm.e0;
                     vd *= sm.e0;
+                }
+                if (c == 0) vd = 1.0;  // no conditioning set: the term is the joint CDF itself
+                if constexpr (MIXED) {
                     // the fast form is exact to 2^-22 only for means >= 2^-40
                     if (MODE == kModeFast && !(vn >= 0x1p-40 && vd >= 0x1p-40 && isfinite(vn) && isfinite(vd)))
                         sm.flag = 1;
                 }
             }
-            Pd.num[site * S + s] = vn;
-            Pd.den[site * S + s] = vd;
+            Pd.num[term * S + s] = vn;
+            Pd.den[term * S + s] = vd;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             if (sm.bad) {
                 ProbResult* R = Pd.res ? Pd.res : &results[item.x];
-                atomicMin((unsigned long long*)&R->bad_site, (unsigned long long)site);
+                atomicMin((unsigned long long*)&R->bad_site, (unsigned long long)term);
                 R->status = (sm.bad == 1) ? VECCHIA_ERR_NOT_PD : VECCHIA_ERR_ARG;
             } else if (MODE == kModeFast && sm.flag && fallback_items) {
                 const int pos = atomicAdd(fallback_count, 1);
@@ -630,7 +745,7 @@ __global__ void __launch_bounds__(kSliceSites) logsum_partial_kernel(
     __shared__ double red[kMaxS + 1][kSliceSites / 32];
     const int pi = blockIdx.y, slice = blockIdx.x;
     const ProbDev& Pd = probs[pi];
-    const int64_t D = Pd.D;
+    const int64_t D = Pd.n_terms;
     const int S = Pd.S;
     if ((int64_t)slice * kSliceSites >= D) return;  // CTA-uniform
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -670,7 +785,7 @@ __global__ void __launch_bounds__(32) logsum_final_kernel(const ProbDev* __restr
                                                           const int64_t* __restrict__ scratch_off) {
     const int pi = blockIdx.x, lane = threadIdx.x;
     const ProbDev& Pd = probs[pi];
-    const int64_t D = Pd.D;
+    const int64_t D = Pd.n_terms;
     const int S = Pd.S;
     if (D <= 0 || S < 2) return;
     const int slices = (int)((D + kSliceSites - 1) / kSliceSites);
@@ -709,23 +824,6 @@ __global__ void init_results_kernel(ProbResult* r, int n, int* fallback_count) {
 }
 
 // ------------------------------- shifts -------------------------------------
-
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        if (round > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
-        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0;
-        c[1] = lo1;
-        c[2] = n2;
-        c[3] = lo0;
-    }
-}
 
 __global__ void shifts_kernel(const uint64_t* __restrict__ seeds, const int32_t* __restrict__ Ss,
                               const int64_t* __restrict__ off, int n_probs, int dim,
@@ -775,23 +873,42 @@ cudaError_t launch_eval_special(int which, const float* x, int64_t n, float* out
 namespace {
 
 template <int DMAX, int P, int MODE>
-cudaError_t launch_one(const GenzTile& tile, const ProbDev* probs, const ItemSrc& src,
+cudaError_t launch_one(const GenzTile& tile, const ProbDev* probs, const ItemSrc& src, int max_S,
                        ProbResult* results, int* fb_count, int2* fb_items, cudaStream_t st) {
     auto kern = genz_kernel<DMAX, P, MODE>;
-    static int per_sm[kMaxWarps + 1] = {0};
-    const int warps = tile.warps < 1 ? 1 : (tile.warps > kMaxWarps ? kMaxWarps : tile.warps);
+    constexpr bool MIXED = MODE != kModeFP64;
+    constexpr int kWarpCap = max_threads(DMAX, P, MODE) / 32;
+    const int warps = tile.warps < 1 ? 1 : (tile.warps > kWarpCap ? kWarpCap : tile.warps);
+    const size_t smem = smem_bytes<DMAX, MIXED>(max_S < 1 ? 1 : max_S, warps);
     int dev = 0;
     cudaGetDevice(&dev);
-    if (per_sm[warps] == 0) {
-        int b = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, warps * 32, 0);
-        if (e != cudaSuccess) return e;
-        per_sm[warps] = b > 0 ? b : 1;
+    // occupancy per (device, warps, shared bytes); the attribute once per device
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, size_t>, int> per_sm;
+    static std::map<int, size_t> attr_set;
+    int blocks_per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto& a = attr_set[dev];
+        if (smem > 48 * 1024 && a < smem) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            a = smem;
+        }
+        auto key = std::make_tuple(dev, warps, smem);
+        auto it = per_sm.find(key);
+        if (it == per_sm.end()) {
+            int b = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, warps * 32, smem);
+            if (e != cudaSuccess) return e;
+            it = per_sm.emplace(key, b > 0 ? b : 1).first;
+        }
+        blocks_per_sm = it->second;
     }
-    const int64_t cap = (int64_t)per_sm[warps] * device_sm_count(dev);
+    const int64_t cap = (int64_t)blocks_per_sm * device_sm_count(dev);
     const int grid = (int)((src.n_items < cap) ? src.n_items : cap);
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, warps * 32, 0, st>>>(probs, src, tile.slices, results, fb_count, fb_items);
+    kern<<<grid, warps * 32, smem, st>>>(probs, src, tile.slices, max_S, results, fb_count, fb_items);
     return cudaGetLastError();
 }
 
@@ -809,13 +926,18 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
     const int per_group = (max_S + t.groups - 1) / t.groups;
     while (t.slices > 1 && per_group * t.slices > kMaxUnits) --t.slices;
     ItemSrc src{nullptr, nullptr, seg_prefix, seg_base, n_segs, n_sites * t.groups, t.groups};
+#define VK_ARGS t, probs, src, max_S, results
 #define VK_CASE(IDX, DM)                                                                         \
     case IDX:                                                                                    \
-        if (!mixed) return launch_one<DM, 1, kModeFP64>(t, probs, src, results, nullptr, nullptr, st); \
+        if (!mixed) return launch_one<DM, 1, kModeFP64>(VK_ARGS, nullptr, nullptr, st);           \
         if (t.points >= 2)                                                                       \
-            return launch_one<DM, 2, kModeFast>(t, probs, src, results, fallback_count, fallback_items, st); \
-        return launch_one<DM, 1, kModeFast>(t, probs, src, results, fallback_count, fallback_items, st);
-    static_assert(kNumBuckets == 7, "bucket table");
+            return launch_one<DM, 2, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);    \
+        return launch_one<DM, 1, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);
+#define VK_CASE1(IDX, DM)                                                                        \
+    case IDX:                                                                                    \
+        if (!mixed) return launch_one<DM, 1, kModeFP64>(VK_ARGS, nullptr, nullptr, st);           \
+        return launch_one<DM, 1, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);
+    static_assert(kNumBuckets == 9, "bucket table");
     switch (bucket) {
         VK_CASE(0, 9)
         VK_CASE(1, 13)
@@ -824,19 +946,25 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
         VK_CASE(4, 25)
         VK_CASE(5, 29)
         VK_CASE(6, 32)
+        VK_CASE1(7, 48)
+        VK_CASE1(8, 64)
         default:
             return cudaErrorInvalidValue;
     }
 #undef VK_CASE
+#undef VK_CASE1
+#undef VK_ARGS
 }
 
-cudaError_t launch_genz_fallback(const ProbDev* probs, const int* fallback_count,
+cudaError_t launch_genz_fallback(int max_bucket, const ProbDev* probs, const int* fallback_count,
                                  const int2* fallback_items, int capacity, ProbResult* results,
-                                 cudaStream_t st) {
+                                 int max_S, cudaStream_t st) {
     if (capacity <= 0) return cudaSuccess;
     GenzTile t{4, 1, 1, 1};
     ItemSrc src{fallback_items, fallback_count, nullptr, nullptr, 0, capacity, 1};
-    return launch_one<32, 1, kModeSafe>(t, probs, src, results, nullptr, nullptr, st);
+    if (max_bucket >= 7)  // blocks of more than 32 variables in the batch
+        return launch_one<64, 1, kModeSafe>(t, probs, src, max_S, results, nullptr, nullptr, st);
+    return launch_one<32, 1, kModeSafe>(t, probs, src, max_S, results, nullptr, nullptr, st);
 }
 
 cudaError_t launch_logsum(const ProbDev* probs, int n_probs, int max_slices, ProbResult* results,

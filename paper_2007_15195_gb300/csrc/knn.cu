@@ -22,7 +22,6 @@
 namespace vk {
 namespace {
 
-constexpr int kMaxQ = 32;
 constexpr int kBruteLimit = 512;
 
 struct Grid {
@@ -135,11 +134,12 @@ __global__ void scatter_kernel(const int2* __restrict__ qxy, int64_t D, const Gr
 
 // ---- warp-wide top-q list -------------------------------------------------
 // A key is (squared quantised distance, index), compared lexicographically.
-// Lane r of a warp holds the r-th smallest key seen so far (r < 32 >= q).
+// The list holds the 32 K smallest keys seen so far (K = 1 or 2 keys per
+// lane): element e = h 32 + lane lives in register h of that lane.
 // Candidates arrive in chunks of up to 32 (one per lane): a chunk is sorted
-// across lanes by a bitonic network, reversed and merged with the list by an
-// element-wise minimum (the 32 smallest of the union form a bitonic sequence),
-// which a bitonic clean-up sorts again.
+// across lanes by a bitonic network, reversed and merged into the top of the
+// list by an element-wise minimum (the 32 K smallest of the union form a
+// bitonic sequence), which a bitonic clean-up sorts again.
 
 struct Key {
     unsigned long long d2;
@@ -150,6 +150,13 @@ constexpr unsigned long long kInfD2 = ~0ULL;
 
 __device__ __forceinline__ bool key_less(const Key& a, const Key& b) {
     return a.d2 < b.d2 || (a.d2 == b.d2 && a.j < b.j);
+}
+
+__device__ __forceinline__ Key inf_key() {
+    Key k;
+    k.d2 = kInfD2;
+    k.j = INT_MAX;
+    return k;
 }
 
 __device__ __forceinline__ Key shfl_key(const Key& k, int src) {
@@ -166,14 +173,24 @@ __device__ __forceinline__ Key shfl_xor_key(const Key& k, int m) {
     return o;
 }
 
-// one compare-exchange stage: partner lane ^ jm; blocks of size kb ascending
-__device__ __forceinline__ void cx(Key& k, int lane, int kb, int jm) {
+// one compare-exchange stage across lanes: partner element e ^ jm (jm < 32);
+// blocks of size kb ascending (kb >= 64 * K: the whole list ascending)
+__device__ __forceinline__ void cx(Key& k, int e, int kb, int jm) {
     const Key o = shfl_xor_key(k, jm);
-    const bool up = (lane & kb) == 0;
-    const bool lower = (lane & jm) == 0;
+    const bool up = (e & kb) == 0;
+    const bool lower = (e & jm) == 0;
     const bool keep_min = (lower == up);
     const bool mine_less = key_less(k, o);
     if (keep_min != mine_less) k = o;
+}
+
+// the compare-exchange of elements lane and lane + 32, both in this lane
+__device__ __forceinline__ void cx_in(Key& lo, Key& hi, bool ascending) {
+    if (key_less(hi, lo) == ascending) {
+        const Key t = lo;
+        lo = hi;
+        hi = t;
+    }
 }
 
 __device__ __forceinline__ void bitonic_sort32(Key& k, int lane) {
@@ -183,13 +200,31 @@ __device__ __forceinline__ void bitonic_sort32(Key& k, int lane) {
         for (int jm = kb >> 1; jm > 0; jm >>= 1) cx(k, lane, kb, jm);
 }
 
-// list (ascending) <- 32 smallest of list and chunk
-__device__ __forceinline__ void merge_chunk(Key& list, Key c, int lane) {
-    bitonic_sort32(c, lane);
-    const Key rev = shfl_key(c, 31 - lane);
-    if (key_less(rev, list)) list = rev;
+// ascending sort of the 64 elements (L[0] at e = lane, L[1] at e = lane + 32)
+__device__ __forceinline__ void bitonic_sort64(Key (&L)[2], int lane) {
+    bitonic_sort32(L[0], lane);  // first half ascending,
 #pragma unroll
-    for (int jm = 16; jm > 0; jm >>= 1) cx(list, lane, 64, jm);  // 64: one ascending block
+    for (int kb = 2; kb <= 32; kb <<= 1)  // second half descending (e & 32 set flips `up`)
+#pragma unroll
+        for (int jm = kb >> 1; jm > 0; jm >>= 1) cx(L[1], lane | 32, kb, jm);
+    cx_in(L[0], L[1], true);  // then one bitonic merge of 64
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int jm = 16; jm > 0; jm >>= 1) cx(L[h], lane + 32 * h, 64, jm);
+}
+
+// list (ascending, 32 K elements) <- the 32 K smallest of list and chunk
+template <int K>
+__device__ __forceinline__ void merge_chunk(Key (&L)[K], Key c, int lane) {
+    bitonic_sort32(c, lane);
+    const Key rev = shfl_key(c, 31 - lane);  // descending chunk against the top 32 of the list
+    if (key_less(rev, L[K - 1])) L[K - 1] = rev;
+    if constexpr (K == 2) cx_in(L[0], L[1], true);
+#pragma unroll
+    for (int h = 0; h < K; ++h)
+#pragma unroll
+        for (int jm = 16; jm > 0; jm >>= 1) cx(L[h], lane + 32 * h, 128, jm);
 }
 
 __device__ __forceinline__ unsigned long long qdist2(int ax, int ay, int bx, int by) {
@@ -199,27 +234,35 @@ __device__ __forceinline__ unsigned long long qdist2(int ax, int ay, int bx, int
 
 constexpr int kSearchWarps = 4;
 
+// One warp per site i: the min(m, lim) nearest sites j < lim, lim = i
+// (group 0) or the first site of i's group of `group` sites.
+template <int K>
 __global__ void __launch_bounds__(32 * kSearchWarps) search_kernel(
-    const int2* __restrict__ qxy, int64_t D, int m, const Grid* __restrict__ grid,
+    const int2* __restrict__ qxy, int64_t D, int m, int group, const Grid* __restrict__ grid,
     const int* __restrict__ offsets, const int4* __restrict__ cell_pts, int32_t* __restrict__ nbr) {
     __shared__ Key stage[kSearchWarps][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t i64 = (int64_t)blockIdx.x * kSearchWarps + wid;
     if (i64 >= D) return;  // warp-uniform
     const int i = (int)i64;
-    const int q = (i < m) ? i : m;
+    const int lim = group > 0 ? (i / group) * group : i;
+    const int q = (lim < m) ? lim : m;
     int32_t* out = nbr + i64 * m;
-    if (q == i) {  // every previous site is a neighbour
-        for (int r = lane; r < m; r += 32) out[r] = (r < i) ? r : -1;
+    if (q == lim) {  // every earlier site is a neighbour
+        for (int r = lane; r < m; r += 32) out[r] = (r < lim) ? r : -1;
         return;
     }
-    Key list;
-    list.d2 = kInfD2;
-    list.j = INT_MAX;
+    Key L[K];
+#pragma unroll
+    for (int h = 0; h < K; ++h) L[h] = inf_key();
     const int2 me = qxy[i];
     Key* st = stage[wid];
     int n = 0;  // staged candidates (warp-uniform)
-    auto worst = [&]() { return shfl_key(list, q - 1); };
+    auto worst = [&]() {  // element q - 1 (q is warp-uniform: no dynamic register index)
+        Key src = L[0];
+        if (K == 2 && q > 32) src = L[K - 1];
+        return shfl_key(src, (q - 1) & 31);
+    };
     // stage the lanes' candidates that beat the current q-th best; merge full chunks
     auto offer = [&](bool valid, Key k) {
         const Key w = worst();
@@ -229,7 +272,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) search_kernel(
         n += __popc(mask);
         __syncwarp();
         if (n >= 32) {
-            merge_chunk(list, st[lane], lane);
+            merge_chunk<K>(L, st[lane], lane);
             __syncwarp();
             if (lane < n - 32) st[lane] = st[32 + lane];
             n -= 32;
@@ -238,27 +281,22 @@ __global__ void __launch_bounds__(32 * kSearchWarps) search_kernel(
     };
     auto flush = [&]() {
         if (n > 0) {
-            Key c;
-            c.d2 = kInfD2;
-            c.j = INT_MAX;
-            if (lane < n) c = st[lane];
-            merge_chunk(list, c, lane);
+            const Key c = (lane < n) ? st[lane] : inf_key();
+            merge_chunk<K>(L, c, lane);
             n = 0;
             __syncwarp();
         }
     };
-    if (i < kBruteLimit) {
-        for (int base = 0; base < i; base += 32) {
+    if (lim < kBruteLimit) {
+        for (int base = 0; base < lim; base += 32) {
             const int j = base + lane;
-            Key k;
-            k.d2 = kInfD2;
-            k.j = INT_MAX;
-            if (j < i) {
+            Key k = inf_key();
+            if (j < lim) {
                 const int2 o = qxy[j];
                 k.d2 = qdist2(me.x, me.y, o.x, o.y);
                 k.j = j;
             }
-            offer(j < i, k);
+            offer(j < lim, k);
         }
         flush();
     } else {
@@ -277,13 +315,11 @@ __global__ void __launch_bounds__(32 * kSearchWarps) search_kernel(
                     const int b = offsets[cell], e = offsets[cell + 1];
                     for (int base = b; base < e; base += 32) {
                         const int p = base + lane;
-                        Key k;
-                        k.d2 = kInfD2;
-                        k.j = INT_MAX;
+                        Key k = inf_key();
                         bool valid = false;
                         if (p < e) {
                             const int4 o = cell_pts[p];
-                            valid = o.z < i;
+                            valid = o.z < lim;
                             k.d2 = qdist2(me.x, me.y, o.x, o.y);
                             k.j = o.z;
                         }
@@ -300,12 +336,100 @@ __global__ void __launch_bounds__(32 * kSearchWarps) search_kernel(
             if (cx0 - r <= 0 && cy0 - r <= 0 && cx0 + r >= G && cy0 + r >= G) break;
         }
     }
-    // lanes < q hold the q nearest; list them ascending by index (Sec. 2.2 block order)
-    Key byj;
-    byj.d2 = 0;
-    byj.j = (lane < q) ? list.j : INT_MAX;
-    bitonic_sort32(byj, lane);
-    if (lane < m) out[lane] = (lane < q) ? byj.j : -1;
+    // elements < q hold the q nearest; list them ascending by index (Sec. 2.2 block order)
+    Key byj[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        byj[h].d2 = 0;
+        byj[h].j = INT_MAX;
+    }
+#pragma unroll
+    for (int h = 0; h < K; ++h)
+        if (lane + 32 * h < q) byj[h].j = L[h].j;
+    if constexpr (K == 1) {
+        bitonic_sort32(byj[0], lane);
+    } else {
+        bitonic_sort64(byj, lane);
+    }
+#pragma unroll
+    for (int h = 0; h < K; ++h) {
+        const int r = lane + 32 * h;
+        if (r < m) out[r] = (r < q) ? byj[h].j : -1;
+    }
+}
+
+// Group k's conditioning row: the union of its members' rows (each ascending),
+// merged by one thread with a p-way merge that drops repeats.
+__global__ void group_union_kernel(const int32_t* __restrict__ per_site, int64_t D, int m, int p, int cmax,
+                                   int32_t* __restrict__ cond, int32_t* __restrict__ count,
+                                   int* __restrict__ overflow) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t G = (D + p - 1) / p;
+    if (k >= G) return;
+    const int64_t i0 = k * p;
+    const int g = (int)((i0 + p < D) ? p : D - i0);
+    int pos[64];
+    for (int a = 0; a < g; ++a) pos[a] = 0;
+    int32_t* row = cond + k * (int64_t)cmax;
+    int n = 0, last = -1;
+    bool over = false;
+    for (;;) {
+        int best = INT_MAX;
+        for (int a = 0; a < g; ++a) {
+            if (pos[a] < m) {
+                const int v = per_site[(i0 + a) * m + pos[a]];
+                if (v >= 0 && v < best) best = v;
+            }
+        }
+        if (best == INT_MAX) break;
+        for (int a = 0; a < g; ++a)  // consume every head equal to best
+            if (pos[a] < m && per_site[(i0 + a) * m + pos[a]] == best) ++pos[a];
+        if (best != last) {
+            if (n < cmax)
+                row[n] = best;
+            else
+                over = true;
+            ++n;
+            last = best;
+        }
+    }
+    for (int r = n; r < cmax; ++r) row[r] = -1;
+    if (count) count[k] = n < cmax ? n : cmax;
+    if (over) atomicExch(overflow, 1);
+}
+
+// Random conditioning: Floyd's algorithm per group (one thread), then an
+// insertion sort of the at most 63 indices.
+__global__ void group_random_kernel(int64_t D, int p, int kk, uint64_t seed, int cmax,
+                                    int32_t* __restrict__ cond, int32_t* __restrict__ count) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t G = (D + p - 1) / p;
+    if (k >= G) return;
+    const int64_t n = k * p;
+    const int take = (int)((kk < n) ? kk : n);
+    int set[64];
+    int have = 0;
+    for (int r = 0; r < take; ++r) {
+        const int64_t j = n - take + r;
+        uint32_t c[4] = {(uint32_t)k, (uint32_t)r, 0x52C5u, (uint32_t)((uint64_t)k >> 32)};
+        philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+        const int t = (int)(((uint64_t)c[0] * (uint64_t)(j + 1)) >> 32);
+        bool dup = false;
+        for (int a = 0; a < have; ++a) dup = dup || set[a] == t;
+        set[have++] = dup ? (int)j : t;
+    }
+    for (int a = 1; a < have; ++a) {
+        const int v = set[a];
+        int b = a - 1;
+        while (b >= 0 && set[b] > v) {
+            set[b + 1] = set[b];
+            --b;
+        }
+        set[b + 1] = v;
+    }
+    int32_t* row = cond + k * (int64_t)cmax;
+    for (int r = 0; r < cmax; ++r) row[r] = (r < have) ? set[r] : -1;
+    if (count) count[k] = have;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -342,7 +466,7 @@ size_t knn_scratch_bytes(int64_t D) {
 }
 
 cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void* scratch,
-                       cudaStream_t st) {
+                       cudaStream_t st, int group) {
     if (D <= 0 || m <= 0) return cudaSuccess;
     const int k = grid_bits(D);
     const int64_t cells = (int64_t)((1 << k) + 1) * ((1 << k) + 1);
@@ -366,8 +490,27 @@ cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void
     quantize_kernel<<<blocks, 256, 0, st>>>(sites, D, grid, qxy, counts);
     scan_kernel<<<1, 1024, 0, st>>>(counts, (int)cells, offsets, cursor);
     scatter_kernel<<<blocks, 256, 0, st>>>(qxy, D, grid, cursor, cell_pts);
-    search_kernel<<<(int)((D + kSearchWarps - 1) / kSearchWarps), 32 * kSearchWarps, 0, st>>>(
-        qxy, D, m, grid, offsets, cell_pts, nbr);
+    const int blocks_s = (int)((D + kSearchWarps - 1) / kSearchWarps);
+    if (m <= 32)
+        search_kernel<1><<<blocks_s, 32 * kSearchWarps, 0, st>>>(qxy, D, m, group, grid, offsets, cell_pts, nbr);
+    else
+        search_kernel<2><<<blocks_s, 32 * kSearchWarps, 0, st>>>(qxy, D, m, group, grid, offsets, cell_pts, nbr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_union(const int32_t* per_site, int64_t D, int m, int p, int cmax, int32_t* cond,
+                               int32_t* count, int* overflow, cudaStream_t st) {
+    const int64_t G = (D + p - 1) / p;
+    if (G <= 0) return cudaSuccess;
+    group_union_kernel<<<(int)((G + 127) / 128), 128, 0, st>>>(per_site, D, m, p, cmax, cond, count, overflow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_random(int64_t D, int p, int kk, uint64_t seed, int cmax, int32_t* cond,
+                                int32_t* count, cudaStream_t st) {
+    const int64_t G = (D + p - 1) / p;
+    if (G <= 0) return cudaSuccess;
+    group_random_kernel<<<(int)((G + 127) / 128), 128, 0, st>>>(D, p, kk, seed, cmax, cond, count);
     return cudaGetLastError();
 }
 

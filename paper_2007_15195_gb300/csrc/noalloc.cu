@@ -64,6 +64,8 @@ bool cov_valid(const vecchia_cov& c) {
     if (!std::isfinite(c.variance) || !std::isfinite(c.range) || !std::isfinite(c.nugget)) return false;
     if (c.kind == VECCHIA_COV_EXPONENTIAL) return true;
     if (c.kind == VECCHIA_COV_MATERN) return c.nu == 0.5 || c.nu == 1.5 || c.nu == 2.5;
+    if (c.kind == VECCHIA_COV_ANISO_EXP)
+        return std::isfinite(c.angle) && std::isfinite(c.aspect) && c.aspect > 0.0;
     return false;
 }
 
@@ -98,7 +100,8 @@ extern "C" int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const doub
     const int bucket = vk::bucket_of(m + 1);
     int groups = 1;
     while (groups < S && (int64_t)groups * D < 4096 && S / (2 * groups) >= 4) groups *= 2;
-    const vk::GenzTile tile{4, (mixed && vk::kDmaxBuckets[bucket] <= 21) ? 2 : 1, 1, groups};
+    vk::GenzTile tile{4, (mixed && vk::kDmaxBuckets[bucket] <= 21) ? 2 : 1, 1, groups};
+    if (vk::kDmaxBuckets[bucket] > 32) tile = vk::GenzTile{8, 1, 1, 1};
 
     // scratch layout (every offset a multiple of 256 bytes)
     size_t off = 0;
@@ -153,13 +156,18 @@ extern "C" int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const doub
     P.delta = (const double*)(base + o_delta);
     P.dfix = (const uint32_t*)(base + o_dfix);
     P.D = D;
+    P.n_terms = D;
     P.N = N;
     P.variance = cov.variance;
     P.range = cov.range;
     P.nu = cov.nu;
     P.nugget = cov.nugget;
     P.cov_kind = cov.kind;
+    P.cos_a = (cov.kind == VECCHIA_COV_ANISO_EXP) ? std::cos(cov.angle) : 1.0;
+    P.sin_a = (cov.kind == VECCHIA_COV_ANISO_EXP) ? std::sin(cov.angle) : 0.0;
+    P.aspect = (cov.kind == VECCHIA_COV_ANISO_EXP) ? cov.aspect : 1.0;
     P.m = m;
+    P.group = 0;
     P.S = S;
     P.dim = kDim;
     h.seed = seed;
@@ -183,7 +191,7 @@ extern "C" int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const doub
         e = vk::launch_genz(bucket, mixed, tile, &dpar->prob, dpar->seg_prefix, dpar->seg_base, 1, (int)D,
                             &dpar->result, fbc, fbi, S, st);
     if (mixed && e == cudaSuccess)
-        e = vk::launch_genz_fallback(&dpar->prob, fbc, fbi, (int)fb_cap, &dpar->result, st);
+        e = vk::launch_genz_fallback(bucket, &dpar->prob, fbc, fbi, (int)fb_cap, &dpar->result, S, st);
     if (e == cudaSuccess)
         e = vk::launch_logsum(&dpar->prob, 1, (int)vk::logsum_slices(D), &dpar->result, nullptr,
                               (double*)(base + o_means), &dpar->means_off, st);

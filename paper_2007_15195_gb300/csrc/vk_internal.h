@@ -13,14 +13,16 @@
 
 namespace vk {
 
-// Bucketed block sizes: a site with q neighbours has d = q + 1 <= 32
-// variables; its problem's Genz kernel is instantiated for the smallest
-// DMAX >= m + 1.  The buckets put m = 8, 12, 16, 20, 24, 28 at the top of
-// theirs, so a lane keeps exactly m partial sums in registers there.
-constexpr int kNumBuckets = 7;
-constexpr int kDmaxBuckets[kNumBuckets] = {9, 13, 17, 21, 25, 29, 32};
+// Bucketed block sizes: a term with d variables (d = q + 1 for a site with q
+// neighbours; d = c + p for a group of p sites conditioned on c) is evaluated
+// by the Genz kernel instantiated for the smallest DMAX >= its problem's
+// largest d.  Up to 32 the buckets put m = 8, 12, ..., 28 at the top of
+// theirs (a lane keeps exactly m partial sums in registers there); 48 and 64
+// take the paper's m = 30 ... 50 and joint groups.
+constexpr int kNumBuckets = 9;
+constexpr int kDmaxBuckets[kNumBuckets] = {9, 13, 17, 21, 25, 29, 32, 48, 64};
 constexpr int kMaxS = VECCHIA_MAX_S;
-constexpr int kMaxDim = 32;  // lattice coordinates per problem (q <= 31)
+constexpr int kMaxDim = 64;  // lattice coordinates per term (d - 1 <= 63)
 
 inline int bucket_of(int d) {
     for (int b = 0; b < kNumBuckets; ++b)
@@ -28,24 +30,32 @@ inline int bucket_of(int d) {
     return -1;
 }
 
+// Largest term dimension of a problem: m + 1 (classic), m + p (groups of p).
+inline int max_term_dim(int m, int group) { return group > 0 ? m + group : m + 1; }
+// Number of Vecchia terms: one per site (classic) or per group of p sites.
+inline int64_t n_terms_of(int64_t D, int group) { return group > 0 ? (D + group - 1) / group : D; }
+
 struct ProbResult;
 
 // One log-CDF problem as the device sees it (all pointers device memory).
 struct ProbDev {
     const double* sites;   // D x 2, ordered
-    const int32_t* nbr;    // D x m
+    const int32_t* nbr;    // n_terms x m conditioning rows (classic: N_i)
     const double* u;       // D
-    double* num;           // D x S partial means (output)
-    double* den;           // D x S
+    double* num;           // n_terms x S partial means (output)
+    double* den;           // n_terms x S
     const uint32_t* g;     // lattice vector, >= m entries
     const double* delta;   // S x dim shifts (FP64)
     const uint32_t* gfix;  // round(g_j 2^32 / N)            (mixed path)
     const uint32_t* dfix;  // top 32 bits of the shift         (mixed path), S x dim
     int64_t D;
+    int64_t n_terms;       // D (classic) or ceil(D / group)
     int64_t N;
     double variance, range, nu, nugget;
+    double cos_a, sin_a, aspect;  // anisotropic exponential: rotation and aspect ratio
     int32_t cov_kind;
     int32_t m;
+    int32_t group;         // 0: classic (term i = site i, N_i = min(m, i) nearest); p: groups of p
     int32_t S;
     int32_t dim;           // row stride of delta / dfix
     ProbResult* res;       // result slot owned by the caller (segment calls), or nullptr
@@ -55,7 +65,7 @@ struct ProbDev {
 struct ProbResult {
     double log_p;
     double std_err;
-    int64_t bad_site;      // first failing ordered site (INT64_MAX if none)
+    int64_t bad_site;      // first failing term (ordered site, or group) (INT64_MAX if none)
     int32_t status;        // VECCHIA_OK or an error code
     int32_t pad;
 };
@@ -70,19 +80,20 @@ struct GenzTile {
 
 // ---------------- kernels' host launchers (genz.cu, knn.cu) ----------------
 
-// Genz partial sums for the sites of one DMAX bucket, given as segments:
-// segment k = sites seg_base[k].y .. of problem seg_base[k].x, with
-// seg_prefix (n_segs + 1 entries, device) the running site count.
+// Genz partial sums for the terms of one DMAX bucket, given as segments:
+// segment k = terms seg_base[k].y .. of problem seg_base[k].x, with
+// seg_prefix (n_segs + 1 entries, device) the running term count.
 cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const ProbDev* probs,
                         const int* seg_prefix, const int2* seg_base, int n_segs, int n_sites,
                         ProbResult* results, int* fallback_count, int2* fallback_items, int max_S,
                         cudaStream_t st);
-// FP64 re-evaluation of the items the mixed kernel flagged (device-side count).
-cudaError_t launch_genz_fallback(const ProbDev* probs, const int* fallback_count,
+// Log-space re-evaluation of the items the mixed kernel flagged (device-side
+// count), instantiated for the largest bucket of the batch.
+cudaError_t launch_genz_fallback(int max_bucket, const ProbDev* probs, const int* fallback_count,
                                  const int2* fallback_items, int capacity, ProbResult* results,
-                                 cudaStream_t st);
-// Per-problem deterministic log-sum and standard error; writes results and
-// terms.  scratch_off[p] points at logsum_scratch(D_p, S_p) doubles.
+                                 int max_S, cudaStream_t st);
+// Per-problem deterministic log-sum and standard error over its n_terms terms;
+// writes results and terms.  scratch_off[p] points at logsum_scratch(n_terms_p, S_p) doubles.
 inline int64_t logsum_slices(int64_t D) { return (D + 255) / 256; }
 inline int64_t logsum_scratch(int64_t D, int S) { return logsum_slices(D) * (S + 1); }
 cudaError_t launch_logsum(const ProbDev* probs, int n_probs, int max_slices, ProbResult* results,
@@ -94,10 +105,21 @@ cudaError_t launch_shifts(const uint64_t* seeds, const int32_t* S, const int64_t
 cudaError_t launch_init_results(ProbResult* results, int n, int* fallback_count, cudaStream_t st);
 
 // Neighbour search for one problem (sites ordered, device); scratch from the
-// caller's arena (bytes from knn_scratch_bytes).
+// caller's arena (bytes from knn_scratch_bytes).  group = 0: the min(m, i)
+// nearest j < i of every site i; group = p: the min(m, i0) nearest j < i0,
+// i0 = (i / p) p the first site of i's group.  m <= 63.
 size_t knn_scratch_bytes(int64_t D);
 cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void* scratch,
-                       cudaStream_t st);
+                       cudaStream_t st, int group = 0);
+// Union of the members' sets (per_site: D x m from launch_knn with group p)
+// into ascending rows of cond (n_groups x cmax, -1 padded) and count; *overflow
+// = 1 if a union has more than cmax entries.
+cudaError_t launch_group_union(const int32_t* per_site, int64_t D, int m, int p, int cmax, int32_t* cond,
+                               int32_t* count, int* overflow, cudaStream_t st);
+// Random conditioning rows: a uniform subset of min(kk, k p) sites before
+// group k (Floyd's algorithm on Philox4x32-10 draws), ascending.
+cudaError_t launch_group_random(int64_t D, int p, int kk, uint64_t seed, int cmax, int32_t* cond,
+                                int32_t* count, cudaStream_t st);
 
 // sites_out[k] = sites[perm[k]], u_out[k] = u[perm[k]]; *bad = 1 on an index out of range.
 cudaError_t launch_gather(const int32_t* perm, const double* sites, const double* u, int64_t D,
@@ -107,5 +129,26 @@ cudaError_t launch_gather(const int32_t* perm, const double* sites, const double
 cudaError_t launch_eval_special(int which, const float* x, int64_t n, float* out, cudaStream_t st);
 
 int device_sm_count(int device);
+
+#ifdef __CUDACC__
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 bijection with
+// the Weyl key schedule, in place on the counter.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+#endif
 
 }  // namespace vk

@@ -257,7 +257,7 @@ def test_argument_errors(ctx):
                               args["precision"])
         assert e.value.status == B.ERR_ARG, b
     with pytest.raises(B.VecchiaError) as e:
-        B.vecchia_neighbors(ctx, s, 32)
+        B.vecchia_neighbors(ctx, s, B.MAX_M + 1)
     assert e.value.status == B.ERR_UNSUPPORTED
     # a neighbour list that is not ascending / not previous
     bad_nbr = nbr.copy()
