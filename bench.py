@@ -38,6 +38,15 @@ UNIT = "evals/s"
 WORKLOAD = ("grid50: D=2500 sites on a 50x50 grid, Matern nu=1.5 range 0.1 variance 1, "
             "u~N(0.5,0.25^2), m=20, N=4096 x S=16, xy order")
 
+
+def metric_for(m):
+    """The headline metric at m = 20; the same measurement at another m says so."""
+    return METRIC if m == 20 else METRIC.replace("m=20", "m=%d" % m)
+
+
+def workload_for(m):
+    return WORKLOAD.replace("m=20", "m=%d" % m)
+
 # FP32-pipe roofline of the Genz kernel (bound "alu").
 #   peak = SMs x 128 FP32 lanes x maximum SM clock (lane operations per second,
 #          an FMA counting as one operation).
@@ -67,7 +76,7 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the error check and cpu_baseline")
     ap.add_argument("--l2-flush-mb", type=int, default=512)
     ap.add_argument("--cpu-sample-sites", type=int, default=160)
-    ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving", "large", "mixture"],
+    ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving", "large", "mixture", "grouped"],
                     help="grid50: the headline line; the others print their own lines")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-rates", default="2000,60", help="arrival rates (req/s) to run")
@@ -178,10 +187,10 @@ def run_reference(args):
         times.append(1.0 / cb["value"])
     t = np.array(times)
     value = len(t) / t.sum()
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_for(args.m), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(t.mean()),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)"},
+            "data": "synthetic", "config": {"workload": workload_for(args.m), "precision": "fp64 (oracle)"},
             "p50_ms": 1000.0 * float(np.percentile(t, 50)), "p99_ms": 1000.0 * float(np.percentile(t, 99)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
@@ -281,10 +290,10 @@ def run_ours(args):
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
     achieved = work / genz_s
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": metric_for(args.m), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 integrand, FP64 Cholesky/sums)",
+            "config": {"workload": workload_for(args.m), "precision": "mixed (FP32 integrand, FP64 Cholesky/sums)",
                        "step": "order+apply_order+neighbors+log_cdf", "seeds": "0..steps-1",
                        "l2": "flushed between steps (%d MB write)" % args.l2_flush_mb,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -537,6 +546,81 @@ def run_mixture(args):
     ctx.close()
 
 
+def run_grouped(args):
+    """Joint-group terms (Sec. 3.2) on the 100x100 grid (exponential range
+    0.1, u ~ N(0.5, 0.25^2), N = 2,048 x S = 8, xy order, mixed precision):
+    groups of p = 2, 5, 10 consecutive sites conditioned on (1) the union of
+    the members' m = 5 nearest earlier sites, (2) m = 5 random earlier sites,
+    (3) p m random earlier sites.  One step = one vecchia_grouped_log_cdf call
+    on resident device arrays, its conditioning rows built once per config
+    (their time is reported beside it).  The line's value is the p = 5,
+    nearest configuration; every configuration is listed."""
+    import torch
+    import paper_2007_15195_gb300 as V
+    from paper_2007_15195_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = V.Context(0, stream.cuda_stream)
+    V.vecchia_set_timing(ctx, True)
+    prob = inputs.grid100()
+    perm = V.vecchia_order(None, prob.sites, prob.order)
+    s, u = V.vecchia_apply_order(None, perm, prob.sites, prob.u)
+    ds, du = torch.from_numpy(s).to(dev), torch.from_numpy(u).to(dev)
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    m = 5
+    rows = []
+    head = None
+    for p in (2, 5, 10):
+        for method, name, k in ((V.COND_NEAREST, "nearest", m), (V.COND_RANDOM, "random m", m),
+                                (V.COND_RANDOM, "random pm", p * m)):
+            cmax = p * m if method == V.COND_NEAREST else k
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cond, cnt = V.vecchia_group_conditioning(ctx, ds, p, k, method, seed=1, cmax=cmax)
+            torch.cuda.synchronize()
+            t_cond = 1000.0 * (time.perf_counter() - t0)
+            run = lambda seed: V.vecchia_grouped_log_cdf(ctx, ds, p, cond, prob.cov, du, prob.N, prob.S,
+                                                         seed=seed, precision=V.MIXED)
+            for w in range(max(args.warmup, 3)):
+                run(10_000 + w)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            genz = []
+            for kk in range(args.steps):
+                ev[kk][0].record(stream)
+                lp, se = run(kk)
+                ev[kk][1].record(stream)
+                genz.append(V.vecchia_genz_time_ms(ctx))
+            torch.cuda.synchronize()
+            ms = np.array([a.elapsed_time(b) for a, b in ev])
+            c = cnt.cpu().numpy().astype(np.float64)
+            G = len(c)
+            gsz = np.minimum(p, prob.D - np.arange(G) * p)
+            d = c + gsz
+            steps = prob.N * prob.S * float(np.sum(d - 1))
+            work = prob.N * prob.S * float(np.sum((d - 1) * ALG_OPS_STEP + (d - 1) * d / 2.0))
+            gk = float(np.median(genz)) / 1000.0
+            row = {"p": p, "method": name, "cond_size_mean": float(c.mean()), "max_dim": int(d.max()),
+                   "ms_per_eval": float(ms.mean()), "p50_ms": float(np.percentile(ms, 50)),
+                   "p99_ms": float(np.percentile(ms, 99)), "cond_ms": t_cond, "log_p": lp, "std_err": se,
+                   "genz_steps": steps, "alu_frac": work / gk / peak}
+            rows.append(row)
+            if p == 5 and method == V.COND_NEAREST:
+                head = row
+    line = {"metric": "grouped Vecchia log-CDF evals/s (100x100 grid, groups of 5, nearest m=5)",
+            "value": 1000.0 / head["ms_per_eval"], "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_eval"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "grouped: 100x100 grid, exponential range 0.1, u~N(0.5,0.25^2), "
+                                   "N=2048 x S=8, xy order, p in {2,5,10}, m=5", "precision": "mixed",
+                       "step": "vecchia_grouped_log_cdf on resident device arrays"},
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "configs": rows}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -549,6 +633,8 @@ def main():
         run_large(args)
     elif args.workload == "mixture":
         run_mixture(args)
+    elif args.workload == "grouped":
+        run_grouped(args)
     else:
         run_ours(args)
 

@@ -72,6 +72,16 @@ def grid50(m: int = 20, seed: int = 0, workload_seed: int = 0, N: int = 4096, S:
                    name="grid50_matern1.5_m%d" % m)
 
 
+def grid100(seed: int = 0, workload_seed: int = 0, N: int = 2048, S: int = 8) -> Problem:
+    """100x100 grid (the joint-group experiment's grid, Sec. 3.2), exponential
+    range 0.1 with unit variance, u_i ~ N(0.5, 0.25^2), N = 2,048 x S = 8.
+    m is set by the caller (per group member)."""
+    s = grid_sites(100)
+    u = rng(workload_seed, _STREAM_U).normal(0.5, 0.25, size=10000)
+    return Problem(s, u, (COV_EXPONENTIAL, 1.0, 0.1, 0.5, 0.0), m=0, N=N, S=S, seed=seed, order="xy",
+                   name="grid100_exp0.1")
+
+
 def batch_problems(n_problems: int = 4096, workload_seed: int = 0, m: int = 20, N: int = 2048,
                    S: int = 8, d_lo: float = 50.0, d_hi: float = 2000.0) -> List[Problem]:
     """Independent problems: D log-uniform in [d_lo, d_hi], sites uniform in the
