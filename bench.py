@@ -252,7 +252,8 @@ def run_ours(args):
     # warm-up (also builds the lattice tables and grows the arena)
     for k in range(max(args.warmup, 3)):
         step(10_000 + k, V.MIXED)
-    step(20_000, V.FP64)
+    if args.fp64_steps > 0:
+        step(20_000, V.FP64)
 
     with ClockSampler(local) as clk:
         ms, genz_ms, res_mixed, wall = timed(args.steps, V.MIXED, 0)
@@ -453,8 +454,13 @@ def run_large(args):
     for nu in (1.5, 0.5):
         prob = inputs.large(nu=nu)
         t0 = time.perf_counter()
-        perm = V.vecchia_order(None, prob.sites, "maxmin")
+        perm_h = V.vecchia_order(None, prob.sites, "maxmin")  # host, all cores
+        t_order_host = time.perf_counter() - t0
+        V.vecchia_order(ctx, prob.sites[:2048], "maxmin")  # warm-up
+        t0 = time.perf_counter()
+        perm = V.vecchia_order(ctx, prob.sites, "maxmin")  # device
         t_order = time.perf_counter() - t0
+        same_order = bool(np.array_equal(perm, perm_h))
         s, u = V.vecchia_apply_order(None, perm, prob.sites, prob.u)
         ds, du = torch.from_numpy(s).to(dev), torch.from_numpy(u).to(dev)
         nbr = V.vecchia_neighbors(ctx, ds, prob.m)
@@ -487,6 +493,7 @@ def run_large(args):
                 "config": {"workload": "large: D=100000 uniform, maxmin, Matern nu=%g range 0.05, u~U[0,2], "
                                        "m=30, N=8192 x S=16" % nu, "precision": "mixed"},
                 "ms_per_eval": float(np.mean(ms)), "log_p": lp, "std_err": se, "order_s": t_order,
+                "order_host_s": t_order_host, "order_device_equals_host": same_order,
                 "neighbors_ms": 1000.0 * t_knn, "genz_steps": steps,
                 "fp64_prefix": {"sites": K, "s": t64, "log_p": lp64,
                                 "est_full_s": t64 * steps / steps_pre},

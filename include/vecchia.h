@@ -95,8 +95,14 @@ int vecchia_set_stream(vecchia_ctx* ctx, void* cuda_stream);
 /* Step a0 -- ordering of the sites (Sec. 2.1; Sec. 3.2 "ordering the
  * components by distance").  perm[new position] = old index (D int32, host or
  * device).  The caller applies perm to sites and u before the next calls.
- * The ordering runs on the host; ctx may be NULL when both arrays are host
- * memory.  MAXMIN costs O(D^2) integer work spread over the host's cores. */
+ * With ctx = NULL both arrays are host memory and the ordering runs on the
+ * host (MAXMIN: O(D^2) integer work over the host's cores).  With a context,
+ * MAXMIN runs on the device (one persistent CTA: a tournament tree over the
+ * distances to the chosen set, each pick scanning only the grid cells within
+ * the current maximum distance), with the same result; XY and IDENTITY stay
+ * on the host.  MAXMIN: first the site nearest the centre of the quantised
+ * bounding box, then repeatedly the site farthest from the chosen ones, on
+ * quantised coordinates, ties to the smaller index. */
 int vecchia_order(vecchia_ctx* ctx, const double* sites, int64_t D, int kind, int32_t* perm);
 
 /* Apply an ordering: sites_out[k] = sites[perm[k]] (D x 2) and, when u is not

@@ -926,9 +926,35 @@ int vecchia_order(vecchia_ctx* c, const double* sites, int64_t D, int kind, int3
     if (!sites || !perm || D < 1 || D > INT_MAX) return VECCHIA_ERR_ARG;
     if (kind != VECCHIA_ORDER_XY && kind != VECCHIA_ORDER_MAXMIN && kind != VECCHIA_ORDER_IDENTITY)
         return VECCHIA_ERR_ARG;
-    // the ordering itself is host work: with no context, both arrays are host memory
+    // with no context both arrays are host memory and the ordering runs on the host
     const bool dev_in = c && is_device_ptr(sites), dev_out = c && is_device_ptr(perm);
     if (c && (dev_in || dev_out) && cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    if (c && kind == VECCHIA_ORDER_MAXMIN) {  // exact maxmin on the device
+        if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+        Carve dv(nullptr);
+        const size_t o_s = dv.off;
+        if (!dev_in) dv.take<double>(2 * D);
+        const size_t o_p = dv.off;
+        if (!dev_out) dv.take<int32_t>(D);
+        const size_t o_scr = dv.off;
+        dv.take<char>(vk::maxmin_scratch_bytes(D));
+        int st = ensure_arena(c, dv.off);
+        if (st != VECCHIA_OK) return st;
+        char* A = (char*)c->arena;
+        const double* sd = dev_in ? sites : (const double*)(A + o_s);
+        int32_t* pd = dev_out ? perm : (int32_t*)(A + o_p);
+        cudaError_t e = cudaSuccess;
+        if (!dev_in) e = cudaMemcpyAsync(A + o_s, sites, sizeof(double) * 2 * D, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = vk::launch_maxmin(sd, D, pd, A + o_scr, c->stream);
+        if (e == cudaSuccess && !dev_out)
+            e = cudaMemcpyAsync(perm, pd, sizeof(int32_t) * D, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return VECCHIA_ERR_CUDA;
+        }
+        return VECCHIA_OK;
+    }
     std::vector<double> hs;
     const double* s = sites;
     if (dev_in) {

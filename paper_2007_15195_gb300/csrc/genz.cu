@@ -62,6 +62,14 @@ __device__ __forceinline__ double cov_fn(int kind, double var, double range, dou
     return var * (1.0 + a + a * a / 3.0) * exp(-a);
 }
 
+// Entry e of a packed lower triangle (row-major: e = r (r + 1) / 2 + c, c <= r).
+__device__ __forceinline__ void tri_index(int e, int& r, int& c) {
+    r = (int)((sqrtf((float)(8 * e + 1)) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    while (r * (r + 1) / 2 > e) --r;
+    c = e - r * (r + 1) / 2;
+}
+
 // Shared memory of a CTA: this fixed part, then (mixed path) the dynamic
 // tail dfix[S][DMAX] (the shifts in 32-bit fixed point) and
 // stepw[warps][DMAX] (per warp, the step constants of its current shift).
@@ -558,36 +566,39 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
                     sm.bu[v] = Pd.u[idx];
                 }
             __syncwarp();
+            // covariance, lower triangle, entries packed over the lanes
             if (!bad)
-                for (int r = lane; r < d; r += 32)
-                    for (int col = 0; col <= r; ++col) {
-                        const double h = site_dist(Pd, __dsub_rn(sm.bx[r], sm.bx[col]), __dsub_rn(sm.by[r], sm.by[col]));
-                        double v = cov_fn(Pd.cov_kind, Pd.variance, Pd.range, Pd.nu, h);
-                        if (col == r) v += Pd.nugget;
-                        sm.A[r][col] = v;
-                    }
-            __syncwarp();
-            // Cholesky, column by column, lanes over rows; every entry's inner
-            // sum runs in ascending k with fma, as in the row-by-row definition.
-            for (int j = 0; j < d && !bad; ++j) {
-                bool piv_ok = true;
-                if (lane == (j & 31)) {
-                    double s = sm.A[j][j];
-                    for (int k = 0; k < j; ++k) s = fma(-sm.A[j][k], sm.A[j][k], s);
-                    piv_ok = s > 0.0;
-                    sm.A[j][j] = sqrt(s);
+                for (int e = lane; e < d * (d + 1) / 2; e += 32) {
+                    int r, col;
+                    tri_index(e, r, col);
+                    const double h = site_dist(Pd, __dsub_rn(sm.bx[r], sm.bx[col]), __dsub_rn(sm.by[r], sm.by[col]));
+                    double v = cov_fn(Pd.cov_kind, Pd.variance, Pd.range, Pd.nu, h);
+                    if (col == r) v += Pd.nugget;
+                    sm.A[r][col] = v;
                 }
-                if (!__shfl_sync(0xffffffffu, (int)piv_ok, j & 31)) {
+            __syncwarp();
+            // Cholesky, right-looking: after column j is final, the trailing
+            // triangle takes its update fma(-L_rj, L_cj, A_rc), entries packed
+            // over the lanes.  Each entry thus receives its terms in ascending
+            // k with fma and is divided by the pivot last: the operations of
+            // the row-by-row definition, in its order.
+            for (int j = 0; j < d && !bad; ++j) {
+                const double s = sm.A[j][j];
+                if (!(s > 0.0)) {  // warp-uniform: every lane reads the same value
                     bad = 1;
                     break;
                 }
+                const double piv = sqrt(s);
+                for (int r = j + 1 + lane; r < d; r += 32) sm.A[r][j] = sm.A[r][j] / piv;
                 __syncwarp();
-                for (int r = lane; r < d; r += 32)
-                    if (r > j) {
-                        double s = sm.A[r][j];
-                        for (int k = 0; k < j; ++k) s = fma(-sm.A[r][k], sm.A[j][k], s);
-                        sm.A[r][j] = s / sm.A[j][j];
-                    }
+                if (lane == 0) sm.A[j][j] = piv;
+                const int n = d - 1 - j;
+                for (int e = lane; e < n * (n + 1) / 2; e += 32) {
+                    int a, b;
+                    tri_index(e, a, b);
+                    const int r = j + 1 + a, col = j + 1 + b;
+                    sm.A[r][col] = fma(-sm.A[r][j], sm.A[col][j], sm.A[r][col]);
+                }
                 __syncwarp();
             }
             if (lane == 0) {
@@ -607,14 +618,18 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
 
         if (!sm.bad) {
             // ---- derived tables for the recursion ----
+            // (mixed: each row scaled by 1/L_vv, one FP64 reciprocal per row)
             constexpr int LS = GenzSmem<DMAX, MIXED>::LS;
             const int d = q + 1;
+            for (int v = threadIdx.x; v < DMAX; v += blockDim.x)
+                sm.diag[v] = (v < d) ? (MIXED ? 1.0 / sm.A[v][v] : sm.A[v][v]) : 0.0;
+            __syncthreads();
             for (int x = threadIdx.x; x < DMAX * LS; x += blockDim.x) {
                 const int t = x / LS, r = x % LS, v = t + 2 + r;
                 T val = (T)0;
                 if (t < q && v < d) {
                     if constexpr (MIXED)
-                        val = (T)(sm.A[v][t] / sm.A[v][v]);
+                        val = (T)(sm.A[v][t] * sm.diag[v]);
                     else
                         val = sm.A[v][t];
                 }
@@ -624,14 +639,13 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
                 T val = (T)0, lz = (T)0;
                 if (v < d) {
                     if constexpr (MIXED)
-                        val = (T)(sm.bu[v] / sm.A[v][v]);
+                        val = (T)(sm.bu[v] * sm.diag[v]);
                     else
                         val = sm.bu[v];
-                    sm.diag[v] = sm.A[v][v];
                 }
                 if (v < q) {
                     if constexpr (MIXED)
-                        lz = (T)(sm.A[v + 1][v] / sm.A[v + 1][v + 1]);
+                        lz = (T)(sm.A[v + 1][v] * sm.diag[v + 1]);
                     else
                         lz = sm.A[v + 1][v];
                 }

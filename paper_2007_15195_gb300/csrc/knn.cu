@@ -16,6 +16,8 @@
 //     best squared distance is below (r*cell + 1)^2;
 //   - sites with a small index are searched by brute force over j < i.
 #include <climits>
+#include <map>
+#include <mutex>
 
 #include "vk_internal.h"
 
@@ -465,9 +467,16 @@ size_t knn_scratch_bytes(int64_t D) {
            3 * align256(sizeof(int) * (size_t)(cells + 1)) + align256(sizeof(int4) * (size_t)D);
 }
 
-cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void* scratch,
-                       cudaStream_t st, int group) {
-    if (D <= 0 || m <= 0) return cudaSuccess;
+// The cell grid of a problem in the caller's scratch (knn_scratch_bytes(D)):
+// bounding box, quantised coordinates, cell offsets and the sites sorted by cell.
+struct Cells {
+    Grid* grid;
+    int2* qxy;
+    int* offsets;
+    int4* cell_pts;
+};
+
+cudaError_t build_cells(const double* sites, int64_t D, void* scratch, cudaStream_t st, Cells& out) {
     const int k = grid_bits(D);
     const int64_t cells = (int64_t)((1 << k) + 1) * ((1 << k) + 1);
     char* p = (char*)scratch;
@@ -482,7 +491,7 @@ cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void
     int* cursor = (int*)p;
     p += align256(sizeof(int) * (size_t)(cells + 1));
     int4* cell_pts = (int4*)p;
-
+    out = Cells{grid, qxy, offsets, cell_pts};
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)cells, st);
     if (e != cudaSuccess) return e;
     bbox_kernel<<<1, 1024, 0, st>>>(sites, D, k, grid);
@@ -490,11 +499,316 @@ cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void
     quantize_kernel<<<blocks, 256, 0, st>>>(sites, D, grid, qxy, counts);
     scan_kernel<<<1, 1024, 0, st>>>(counts, (int)cells, offsets, cursor);
     scatter_kernel<<<blocks, 256, 0, st>>>(qxy, D, grid, cursor, cell_pts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void* scratch,
+                       cudaStream_t st, int group) {
+    if (D <= 0 || m <= 0) return cudaSuccess;
+    Cells c;
+    cudaError_t e = build_cells(sites, D, scratch, st, c);
+    if (e != cudaSuccess) return e;
     const int blocks_s = (int)((D + kSearchWarps - 1) / kSearchWarps);
     if (m <= 32)
-        search_kernel<1><<<blocks_s, 32 * kSearchWarps, 0, st>>>(qxy, D, m, group, grid, offsets, cell_pts, nbr);
+        search_kernel<1><<<blocks_s, 32 * kSearchWarps, 0, st>>>(c.qxy, D, m, group, c.grid, c.offsets,
+                                                                  c.cell_pts, nbr);
     else
-        search_kernel<2><<<blocks_s, 32 * kSearchWarps, 0, st>>>(qxy, D, m, group, grid, offsets, cell_pts, nbr);
+        search_kernel<2><<<blocks_s, 32 * kSearchWarps, 0, st>>>(c.qxy, D, m, group, c.grid, c.offsets,
+                                                                  c.cell_pts, nbr);
+    return cudaGetLastError();
+}
+
+// ---- exact maxmin ordering (one persistent CTA) ----------------------------
+// Same rule as the host ordering: first the site nearest the centre of the
+// quantised bounding box (2q - qmax, smallest squared distance, ties to the
+// smaller index), then repeatedly the unchosen site whose squared distance to
+// the chosen set is largest (ties to the smaller index).  mind[i] holds that
+// distance (-1 once chosen); a 32-ary tournament tree over (mind, index) gives
+// the next pick at its root.  A pick at max distance r^2 can only lower the
+// mind of sites closer than r, so each step scans the grid cells within r of
+// the pick and recomputes the tree nodes above the leaves that changed.
+
+constexpr int kMmThreads = 1024;
+constexpr int kMmMaxLevels = 8;
+
+struct MmTree {
+    long long* val;   // node values, all levels (level l at off[l])
+    int* idx;         // node argmax index
+    int* flag;        // dirty marks
+    int* list[2];     // dirty node lists (alternating)
+    int off[kMmMaxLevels + 1];
+    int n[kMmMaxLevels + 1];  // n[0] = D leaves, n[l] nodes of level l
+    int levels;               // root = level `levels`, node 0
+    int total;                // nodes of all levels
+    int in_smem;              // 1: the arrays live in the CTA's dynamic shared memory
+};
+
+__device__ __forceinline__ bool mm_better(long long va, int ia, long long vb, int ib) {
+    return va > vb || (va == vb && ia < ib);
+}
+
+__device__ __forceinline__ void mm_warp_argmax(long long& v, int& i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (mm_better(ov, oi, v, i)) {
+            v = ov;
+            i = oi;
+        }
+    }
+}
+
+// Bytes of the tree arrays (8 + 4 + 4 per node, two lists of level-1 size).
+__host__ __device__ inline size_t mm_tree_bytes(int total, int n1) {
+    return (size_t)total * 16 + (size_t)2 * n1 * 4 + 64;
+}
+
+// Node `node` of level l (>= 1): argmax of its 32 children; lane 0 stores it,
+// clears its mark and queues its parent.
+__device__ __forceinline__ void mm_node(MmTree& T, const long long* mind, int l, int node, int* cnt, int lane) {
+    const int c = node * 32 + lane;
+    long long v = LLONG_MIN;
+    int i = INT_MAX;
+    if (c < T.n[l - 1]) {
+        if (l == 1) {
+            v = mind[c];
+            i = c;
+        } else {
+            v = T.val[T.off[l - 1] + c];
+            i = T.idx[T.off[l - 1] + c];
+        }
+    }
+    mm_warp_argmax(v, i);
+    if (lane == 0) {
+        T.val[T.off[l] + node] = v;
+        T.idx[T.off[l] + node] = i;
+        T.flag[T.off[l] + node] = 0;
+        if (l < T.levels) {
+            const int parent = node >> 5;
+            if (atomicExch(&T.flag[T.off[l + 1] + parent], 1) == 0)
+                T.list[(l + 1) & 1][atomicAdd(&cnt[l + 1], 1)] = parent;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kMmThreads) maxmin_kernel(const Grid* __restrict__ grid,
+                                                            const int2* __restrict__ qxy,
+                                                            const int* __restrict__ offsets,
+                                                            const int4* __restrict__ cell_pts, int D,
+                                                            long long* __restrict__ mind, MmTree T,
+                                                            int32_t* __restrict__ perm) {
+    extern __shared__ __align__(16) unsigned char mm_smem[];
+    __shared__ long long red_v[kMmThreads / 32], red_y[kMmThreads / 32];
+    __shared__ int red_i[kMmThreads / 32];
+    __shared__ int cnt[kMmMaxLevels + 2];
+    __shared__ int s_pick;
+    __shared__ long long s_r2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Grid g = *grid;
+    const int W = g.G + 1;
+    if (T.in_smem) {  // carve the tree out of dynamic shared memory
+        unsigned char* p = mm_smem;
+        T.val = (long long*)p;
+        p += (size_t)T.total * 8;
+        T.idx = (int*)p;
+        p += (size_t)T.total * 4;
+        T.flag = (int*)p;
+        p += (size_t)T.total * 4;
+        T.list[0] = (int*)p;
+        p += (size_t)T.n[1] * 4;
+        T.list[1] = (int*)p;
+    }
+
+    // leaves at "infinity", no marks
+    for (int i = tid; i < D; i += kMmThreads) mind[i] = LLONG_MAX;
+    for (int x = tid; x < T.total; x += kMmThreads) T.flag[x] = 0;
+    // the first site: nearest the centre of the quantised bounding box
+    long long qxm = 0, qym = 0;
+    for (int i = tid; i < D; i += kMmThreads) {
+        qxm = max(qxm, (long long)qxy[i].x);
+        qym = max(qym, (long long)qxy[i].y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        qxm = max(qxm, __shfl_xor_sync(0xffffffffu, qxm, o));
+        qym = max(qym, __shfl_xor_sync(0xffffffffu, qym, o));
+    }
+    if (lane == 0) {
+        red_v[warp] = qxm;
+        red_y[warp] = qym;
+    }
+    __syncthreads();
+    qxm = 0;
+    qym = 0;
+    for (int w = 0; w < kMmThreads / 32; ++w) {
+        qxm = max(qxm, red_v[w]);
+        qym = max(qym, red_y[w]);
+    }
+    __syncthreads();
+    long long bv = LLONG_MAX;
+    int bi = INT_MAX;
+    for (int i = tid; i < D; i += kMmThreads) {
+        const long long dx = 2LL * qxy[i].x - qxm, dy = 2LL * qxy[i].y - qym;
+        const long long v = dx * dx + dy * dy;
+        if (v < bv || (v == bv && i < bi)) {
+            bv = v;
+            bi = i;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {  // arg-min over (distance, index)
+        const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov < bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        red_v[warp] = bv;
+        red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long v = LLONG_MAX;
+        int f = INT_MAX;
+        for (int w = 0; w < kMmThreads / 32; ++w)
+            if (red_v[w] < v || (red_v[w] == v && red_i[w] < f)) {
+                v = red_v[w];
+                f = red_i[w];
+            }
+        perm[0] = f;
+        mind[f] = -1;
+        s_pick = f;
+        s_r2 = LLONG_MAX;  // every site is within reach of the first pick
+        for (int l = 0; l < kMmMaxLevels + 2; ++l) cnt[l] = 0;
+        T.flag[T.off[1] + (f >> 5)] = 1;
+        T.list[1][0] = f >> 5;
+        cnt[1] = 1;
+    }
+    __syncthreads();
+
+    for (int k = 1; k < D; ++k) {
+        // scan: lower mind of the sites within reach of the last pick
+        const int pick = s_pick;
+        const long long r2 = s_r2;
+        const int2 pq = qxy[pick];
+        int cx_lo = 0, cx_hi = g.G, cy_lo = 0, cy_hi = g.G;
+        if (r2 != LLONG_MAX) {
+            const long long rr = (long long)sqrt((double)r2) + 1;  // |dx|, |dy| < rr for d^2 < r2
+            cx_lo = (int)(max(0LL, (long long)pq.x - rr) >> g.shift);
+            cy_lo = (int)(max(0LL, (long long)pq.y - rr) >> g.shift);
+            cx_hi = (int)min((long long)g.G, ((long long)pq.x + rr) >> g.shift);
+            cy_hi = (int)min((long long)g.G, ((long long)pq.y + rr) >> g.shift);
+        }
+        for (int row = cy_lo + warp; row <= cy_hi; row += kMmThreads / 32) {
+            const int b = offsets[row * W + cx_lo], e = offsets[row * W + cx_hi + 1];
+            for (int x = b + lane; x < e; x += 32) {
+                const int4 o = cell_pts[x];
+                const long long mi = mind[o.z];
+                if (mi < 0) continue;
+                const long long dx = (long long)o.x - pq.x, dy = (long long)o.y - pq.y;
+                const long long d2 = dx * dx + dy * dy;
+                if (d2 < mi) {
+                    mind[o.z] = d2;
+                    const int node = o.z >> 5;
+                    if (atomicExch(&T.flag[T.off[1] + node], 1) == 0) T.list[1][atomicAdd(&cnt[1], 1)] = node;
+                }
+            }
+        }
+        __syncthreads();
+        // level 1 by all warps
+        for (int j = warp; j < cnt[1]; j += kMmThreads / 32) mm_node(T, mind, 1, T.list[1][j], cnt, lane);
+        __syncthreads();
+        // upper levels and the next pick by warp 0
+        if (warp == 0) {
+            for (int l = 2; l <= T.levels; ++l) {
+                const int n = cnt[l];
+                for (int j = 0; j < n; ++j) mm_node(T, mind, l, T.list[l & 1][j], cnt, lane);
+                __syncwarp();
+            }
+            if (lane == 0) {
+                const int root = T.off[T.levels];
+                const int nxt = T.idx[root];
+                perm[k] = nxt;
+                mind[nxt] = -1;
+                s_pick = nxt;
+                s_r2 = T.val[root];
+                for (int l = 0; l < kMmMaxLevels + 2; ++l) cnt[l] = 0;
+                T.flag[T.off[1] + (nxt >> 5)] = 1;  // its own leaf changed
+                T.list[1][0] = nxt >> 5;
+                cnt[1] = 1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Tree shape for D leaves: level sizes and offsets.
+bool mm_shape(int64_t D, MmTree& T) {
+    T.n[0] = (int)D;
+    T.off[0] = 0;
+    int levels = 0, total = 0;
+    int64_t n = D;
+    do {
+        n = (n + 31) / 32;
+        ++levels;
+        if (levels > kMmMaxLevels) return false;
+        T.off[levels] = total;
+        T.n[levels] = (int)n;
+        total += (int)n;
+    } while (n > 1);
+    T.levels = levels;
+    T.total = total;
+    return true;
+}
+
+constexpr size_t kMmSmemMax = 200 * 1024;
+
+size_t maxmin_scratch_bytes(int64_t D) {
+    MmTree T;
+    if (!mm_shape(D, T)) return 0;
+    return knn_scratch_bytes(D) + align256(sizeof(long long) * (size_t)D) + align256(mm_tree_bytes(T.total, T.n[1]));
+}
+
+cudaError_t launch_maxmin(const double* sites, int64_t D, int32_t* perm, void* scratch, cudaStream_t st) {
+    if (D <= 0) return cudaSuccess;
+    MmTree T;
+    if (!mm_shape(D, T)) return cudaErrorInvalidValue;
+    Cells c;
+    cudaError_t e = build_cells(sites, D, scratch, st, c);
+    if (e != cudaSuccess) return e;
+    char* p = (char*)scratch + knn_scratch_bytes(D);
+    long long* mind = (long long*)p;
+    p += align256(sizeof(long long) * (size_t)D);
+    const size_t tree = mm_tree_bytes(T.total, T.n[1]);
+    T.in_smem = tree <= kMmSmemMax;
+    size_t smem = 0;
+    if (T.in_smem) {
+        smem = tree;
+        static std::mutex mu;
+        static std::map<int, size_t> attr;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(mu);
+        if (smem > 48 * 1024 && attr[dev] < smem) {
+            e = cudaFuncSetAttribute(maxmin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMmSmemMax);
+            if (e != cudaSuccess) return e;
+            attr[dev] = kMmSmemMax;
+        }
+        T.val = nullptr;
+        T.idx = T.flag = T.list[0] = T.list[1] = nullptr;
+    } else {
+        T.val = (long long*)p;
+        p += (size_t)T.total * 8;
+        T.idx = (int*)p;
+        p += (size_t)T.total * 4;
+        T.flag = (int*)p;
+        p += (size_t)T.total * 4;
+        T.list[0] = (int*)p;
+        p += (size_t)T.n[1] * 4;
+        T.list[1] = (int*)p;
+    }
+    maxmin_kernel<<<1, kMmThreads, smem, st>>>(c.grid, c.qxy, c.offsets, c.cell_pts, (int)D, mind, T, perm);
     return cudaGetLastError();
 }
 

@@ -111,6 +111,10 @@ cudaError_t launch_init_results(ProbResult* results, int n, int* fallback_count,
 size_t knn_scratch_bytes(int64_t D);
 cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void* scratch,
                        cudaStream_t st, int group = 0);
+// Exact maxmin ordering on the device (one persistent CTA); perm (D, device)
+// gets new position -> old index; scratch from maxmin_scratch_bytes(D).
+size_t maxmin_scratch_bytes(int64_t D);
+cudaError_t launch_maxmin(const double* sites, int64_t D, int32_t* perm, void* scratch, cudaStream_t st);
 // Union of the members' sets (per_site: D x m from launch_knn with group p)
 // into ascending rows of cond (n_groups x cmax, -1 padded) and count; *overflow
 // = 1 if a union has more than cmax entries.

@@ -179,3 +179,27 @@ def test_malformed_group_row_names_the_group(ctx):
     with pytest.raises(B.VecchiaError) as e:
         B.vecchia_grouped_log_cdf(ctx, s, 3, bad, cov, u, 128, 4, precision=B.MIXED)
     assert e.value.status == B.ERR_ARG and B.vecchia_last_error_site(ctx) == k
+
+
+# ---- exact maxmin ordering on the device (Sec. 3.2 ordering by distance) ----
+
+@pytest.mark.parametrize("D,kind", [(1, "u"), (2, "u"), (33, "u"), (1000, "u"), (2500, "grid"),
+                                    (20000, "u"), (600, "dup")])
+def test_device_maxmin_equals_oracle(ctx, D, kind):
+    import torch
+    if kind == "u":
+        s = inputs.uniform_sites(D, D + 3)
+    elif kind == "grid":
+        s = inputs.grid_sites(int(round(math.sqrt(D))))
+    else:  # every site three times: ties everywhere
+        s = np.repeat(inputs.uniform_sites(D // 3, 8), 3, axis=0)
+    ref = O.order(s, O.ORDER_MAXMIN)
+    got = B.vecchia_order(ctx, s, "maxmin")
+    assert np.array_equal(got, ref)
+    got_d = B.vecchia_order(ctx, torch.from_numpy(s).cuda(), "maxmin")
+    assert np.array_equal(got_d.cpu().numpy(), ref)
+
+
+def test_device_maxmin_equals_host_ordering_at_large_size(ctx):
+    s = inputs.large().sites[:100_000]
+    assert np.array_equal(B.vecchia_order(ctx, s, "maxmin"), B.vecchia_order(None, s, "maxmin"))
