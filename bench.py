@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--m", type=int, default=20)
     ap.add_argument("--no-oracle", action="store_true", help="skip the error check and cpu_baseline")
+    ap.add_argument("--no-full", action="store_true", help="skip the full-dimensional Genz comparison")
     ap.add_argument("--l2-flush-mb", type=int, default=512)
     ap.add_argument("--cpu-sample-sites", type=int, default=160)
     ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving", "large", "mixture", "grouped"],
@@ -315,6 +316,21 @@ def run_ours(args):
             "gpu_launches": launches_per_step[V.MIXED] * args.steps,
             "clocks": clocks}
 
+    if rank == 0 and not args.no_full:
+        # the full-dimensional Genz estimate on the same lattice and shifts
+        # (seed 0): the m = D - 1 limit the approximation is compared with
+        perm_f = V.vecchia_order(ctx, sites_d, "xy")
+        s_f, u_f = V.vecchia_apply_order(ctx, perm_f, sites_d, u_d)
+        full = {}
+        for prec, name in ((V.MIXED, "mixed"), (V.FP64, "fp64")):
+            lp_f, se_f = V.vecchia_full_genz(ctx, s_f, prob.cov, u_f, N, S, seed=0, precision=prec)
+            full[name] = {"log_p": lp_f, "rel_se": se_f, "ms": V.vecchia_genz_time_ms(ctx)}
+        lp_v = res_mixed[0][0]
+        full["vecchia_mixed_log_p"] = lp_v
+        full["vecchia_minus_full"] = lp_v - full["fp64"]["log_p"]
+        full["note"] = ("seed 0; rel_se is the full estimate's relative standard error over the S shifts "
+                        "(near 1: its shifts disagree by orders of magnitude at this D)")
+        line["full_genz"] = full
     if rank == 0 and not args.no_oracle:
         import oracle as O
         perm = O.order(prob.sites, O.ORDER_XY)

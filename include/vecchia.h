@@ -288,6 +288,24 @@ int vecchia_mixture_log_cdf(vecchia_ctx* ctx, const double* sites_ordered, int64
                             int S, uint64_t seed, double beta, double gamma, int n_nodes,
                             int precision, double* log_g, double* std_err);
 
+/* The full D-dimensional Genz estimate of P(X < u) (Sec. 2.2, Sec. 3) on the
+ * same rank-1 lattice (dimension D - 1) and shifts as the Vecchia terms: the
+ * m = D - 1 limit of Eq. (vecchia-cdf), which telescopes (Eq.
+ * cascading-conditional-cdf) -- the estimate the approximation is compared
+ * with.  Covariance and Cholesky in FP64 (blocked; each entry of the factor
+ * takes its terms in ascending order with fma, then the pivot division);
+ * the recursion over all D variables in the precision requested (mixed: FP32
+ * integrand and conditional means, FP64 running product and sums).  log_p =
+ * log of the mean over shifts of the lattice means; rel_se = their standard
+ * error over the mean.  Arrays host or device (both of one kind); device
+ * memory grows as 12 D^2 + 4 (8 for FP64) D S N bytes.  D <= VECCHIA_FULL_MAX_D.
+ * A non-positive pivot gives VECCHIA_ERR_NOT_PD with its site in
+ * vecchia_last_error_site(). */
+#define VECCHIA_FULL_MAX_D 32768
+int vecchia_full_genz(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, vecchia_cov cov,
+                      const double* u, int64_t N, int S, uint64_t seed, int precision, double* log_p,
+                      double* rel_se);
+
 /* Korobov generating vector g[j] = a^j mod N, j < dim (host array): a in
  * [2, N/2], gcd(a, N) = 1, minimising the weighted P2 criterion over 30
  * dimensions with weights 1/j^2 (ties: smaller a).  N < 4 gives a = 1. */

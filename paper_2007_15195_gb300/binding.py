@@ -107,6 +107,8 @@ def lib():
         L.vecchia_grouped_log_cdf.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, C.c_int, vecchia_cov, _vp,
                                               C.c_int64, C.c_int, C.c_uint64, C.c_int, C.POINTER(C.c_double),
                                               C.POINTER(C.c_double)]
+        L.vecchia_full_genz.argtypes = [_vp, _vp, C.c_int64, vecchia_cov, _vp, C.c_int64, C.c_int, C.c_uint64,
+                                        C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.vecchia_lattice.argtypes = [C.c_int64, C.c_int, _vp]
         L.vecchia_shifts.argtypes = [C.c_uint64, C.c_int, C.c_int, _vp]
         L.vecchia_last_error_site.restype = C.c_int64
@@ -302,6 +304,16 @@ def vecchia_grouped_log_cdf(ctx, sites_ordered, p, cond, cov, u, N, S, seed=0, p
                                          make_cov(cov), _ptr(uu), int(N), int(S), C.c_uint64(int(seed)),
                                          int(precision), C.byref(lp), C.byref(se)), "vecchia_grouped_log_cdf",
            ctx)
+    return lp.value, se.value
+
+
+def vecchia_full_genz(ctx, sites_ordered, cov, u, N, S, seed=0, precision=MIXED):
+    """The full D-dimensional Genz estimate: returns (log_p, rel_se)."""
+    s, uu = _f64(sites_ordered), _f64(u)
+    lp, se = C.c_double(), C.c_double()
+    _check(lib().vecchia_full_genz(ctx.handle, _ptr(s), s.shape[0], make_cov(cov), _ptr(uu), int(N), int(S),
+                                   C.c_uint64(int(seed)), int(precision), C.byref(lp), C.byref(se)),
+           "vecchia_full_genz", ctx)
     return lp.value, se.value
 
 

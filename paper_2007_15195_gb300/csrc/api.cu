@@ -1192,6 +1192,80 @@ int vecchia_group_conditioning(vecchia_ctx* c, const double* sites, int64_t D, i
     return h_over ? VECCHIA_ERR_ARG : VECCHIA_OK;
 }
 
+int vecchia_full_genz(vecchia_ctx* c, const double* sites, int64_t D, vecchia_cov cov, const double* u, int64_t N,
+                      int S, uint64_t seed, int precision, double* log_p, double* rel_se) {
+    if (!c || !sites || !u || !log_p || !rel_se || D < 1 || N < 1 || N > INT_MAX) return VECCHIA_ERR_ARG;
+    if (S < 2 || S > VECCHIA_MAX_S || !cov_ok(cov)) return VECCHIA_ERR_ARG;
+    if (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) return VECCHIA_ERR_ARG;
+    if (D > VECCHIA_FULL_MAX_D) return VECCHIA_ERR_UNSUPPORTED;
+    *log_p = NAN;
+    *rel_se = NAN;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    c->last_error_site = -1;
+    const bool mixed = precision == VECCHIA_MIXED;
+    const bool dev_in = is_device_ptr(sites);
+    if (dev_in != is_device_ptr(u)) return VECCHIA_ERR_ARG;
+    const int64_t dim = D > 1 ? D - 1 : 1;
+    std::vector<uint32_t> g((size_t)dim), gfix((size_t)dim);
+    lattice_host(N, (int)dim, g.data());
+    for (int64_t j = 0; j < dim; ++j)  // round(g 2^32 / N)
+        gfix[(size_t)j] = (uint32_t)((((uint64_t)g[(size_t)j] << 32) + (uint64_t)N / 2) / (uint64_t)N);
+    Carve dv(nullptr);
+    const size_t o_s = dv.off;
+    if (!dev_in) dv.take<double>(2 * D);
+    const size_t o_u = dv.off;
+    if (!dev_in) dv.take<double>(D);
+    const size_t o_scr = dv.off;
+    dv.take<char>(vk::full_genz_scratch_bytes(D, N, S, mixed));
+    int st = ensure_arena(c, dv.off);
+    if (st != VECCHIA_OK) return st;
+    char* A = (char*)c->arena;
+    const double* sd = dev_in ? sites : (const double*)(A + o_s);
+    const double* ud = dev_in ? u : (const double*)(A + o_u);
+    const int64_t bps = (N + 127) / 128;
+    std::vector<double> part((size_t)(S * bps));
+    int bad = INT_MAX;
+    cudaError_t e = cudaSuccess;
+    if (!dev_in) e = cudaMemcpyAsync(A + o_s, sites, sizeof(double) * 2 * D, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !dev_in)
+        e = cudaMemcpyAsync(A + o_u, u, sizeof(double) * D, cudaMemcpyHostToDevice, c->stream);
+    if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev0, c->stream);
+    if (e == cudaSuccess)
+        e = vk::launch_full_genz(sd, ud, D, cov, N, S, mixed, g.data(), gfix.data(), seed, A + o_scr, part.data(),
+                                 &bad, c->stream);
+    if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    if (c->timing) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->genz_ms = ms;
+    }
+    if (bad != INT_MAX) {
+        c->last_error_site = bad;
+        return VECCHIA_ERR_NOT_PD;
+    }
+    // per-shift means (tile sums in order), their mean and relative standard error
+    std::vector<double> ps((size_t)S);
+    double mean = 0.0;
+    for (int s = 0; s < S; ++s) {
+        double t = 0.0;
+        for (int64_t b = 0; b < bps; ++b) t += part[(size_t)(s * bps + b)];
+        ps[(size_t)s] = t / (double)N;
+        mean += ps[(size_t)s];
+    }
+    mean /= (double)S;
+    double ss = 0.0;
+    for (int s = 0; s < S; ++s) ss += (ps[(size_t)s] - mean) * (ps[(size_t)s] - mean);
+    *log_p = std::log(mean);
+    *rel_se = std::sqrt(ss / ((double)S * (S - 1))) / mean;
+    if (!std::isfinite(*log_p) || !std::isfinite(*rel_se)) return VECCHIA_ERR_NONFINITE;
+    return VECCHIA_OK;
+}
+
 int vecchia_mixture_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, const int32_t* nbr, int m,
                             vecchia_cov cov, const double* x, int64_t N, int S, uint64_t seed,
                             double beta, double gamma, int n_nodes, int precision, double* log_g,

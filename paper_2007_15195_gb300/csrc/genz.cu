@@ -32,6 +32,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "cov.cuh"
 #include "special_f32.h"
 #include "vk_internal.h"
 
@@ -40,27 +41,6 @@ namespace {
 
 constexpr int kMaxWarps = 16;
 constexpr int kMaxUnits = 64;  // shifts x slices handled by one CTA item
-
-// Distance between two sites: Euclidean, or the Mahalanobis distance of
-// Sec. 4.1 for the anisotropic exponential (explicit roundings, no contraction).
-__device__ __forceinline__ double site_dist(const ProbDev& P, double dx, double dy) {
-    if (P.cov_kind == VECCHIA_COV_ANISO_EXP) {
-        const double o1 = __dsub_rn(__dmul_rn(dx, P.cos_a), __dmul_rn(dy, P.sin_a));
-        const double o2 = __dmul_rn(P.aspect, __dadd_rn(__dmul_rn(dx, P.sin_a), __dmul_rn(dy, P.cos_a)));
-        return sqrt(__dadd_rn(__dmul_rn(o1, o1), __dmul_rn(o2, o2)));
-    }
-    return sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-}
-
-__device__ __forceinline__ double cov_fn(int kind, double var, double range, double nu, double h) {
-    if (kind != VECCHIA_COV_MATERN || nu == 0.5) return var * exp(-h / range);
-    if (nu == 1.5) {
-        const double a = 1.7320508075688772935 * h / range;
-        return var * (1.0 + a) * exp(-a);
-    }
-    const double a = 2.2360679774997896964 * h / range;
-    return var * (1.0 + a + a * a / 3.0) * exp(-a);
-}
 
 // Entry e of a packed lower triangle (row-major: e = r (r + 1) / 2 + c, c <= r).
 __device__ __forceinline__ void tri_index(int e, int& r, int& c) {

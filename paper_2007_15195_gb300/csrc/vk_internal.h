@@ -125,6 +125,14 @@ cudaError_t launch_group_union(const int32_t* per_site, int64_t D, int m, int p,
 cudaError_t launch_group_random(int64_t D, int p, int kk, uint64_t seed, int cmax, int32_t* cond,
                                 int32_t* count, cudaStream_t st);
 
+// Full D-dimensional Genz estimate (full.cu): covariance, blocked FP64
+// Cholesky, Genz over all variables; part_host gets S x ceil(N/128) tile sums
+// of the point products, *bad_host the first non-positive pivot (INT_MAX if none).
+size_t full_genz_scratch_bytes(int64_t D, int64_t N, int S, bool mixed);
+cudaError_t launch_full_genz(const double* sites, const double* u, int64_t D, const vecchia_cov& cov, int64_t N,
+                             int S, bool mixed, const uint32_t* g_host, const uint32_t* gfix_host,
+                             uint64_t seed, void* scratch, double* part_host, int* bad_host, cudaStream_t st);
+
 // sites_out[k] = sites[perm[k]], u_out[k] = u[perm[k]]; *bad = 1 on an index out of range.
 cudaError_t launch_gather(const int32_t* perm, const double* sites, const double* u, int64_t D,
                           double* sites_out, double* u_out, int* bad, cudaStream_t st);

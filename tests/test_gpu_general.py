@@ -203,3 +203,38 @@ def test_device_maxmin_equals_oracle(ctx, D, kind):
 def test_device_maxmin_equals_host_ordering_at_large_size(ctx):
     s = inputs.large().sites[:100_000]
     assert np.array_equal(B.vecchia_order(ctx, s, "maxmin"), B.vecchia_order(None, s, "maxmin"))
+
+
+# ---- full D-dimensional Genz (the m = D - 1 limit) --------------------------
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
+@pytest.mark.parametrize("D,N,S", [(1, 256, 4), (2, 256, 4), (150, 512, 4), (600, 300, 4)])
+def test_full_genz_against_oracle(ctx, prec, D, N, S):
+    s, u, cov = _ordered(D, 500 + D, cov=(O.COV_EXPONENTIAL, 1.0, 0.3, 0.5, 0.0))
+    ref, ref_se = O.full_genz(s, cov, u, N, S, 3)
+    lp, se = B.vecchia_full_genz(ctx, s, cov, u, N, S, seed=3, precision=prec)
+    _check(lp, ref, prec)
+    if prec == B.FP64 and D > 1:
+        assert se == pytest.approx(ref_se, rel=1e-6)
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
+def test_full_genz_equals_vecchia_with_every_neighbour(ctx, prec):
+    """Eq. (vecchia-cdf) with m = D - 1 telescopes to the full estimate."""
+    D = 60
+    s, u, cov = _ordered(D, 77, cov=(B.COV_MATERN, 1.0, 0.2, 1.5, 0.0))
+    nbr = B.vecchia_neighbors(ctx, s, D - 1)
+    a, _ = B.vecchia_log_cdf(ctx, s, nbr, D - 1, cov, u, 1024, 8, 5, prec)
+    b, _ = B.vecchia_full_genz(ctx, s, cov, u, 1024, 8, seed=5, precision=prec)
+    assert abs(a - b) <= (1e-10 * abs(b) if prec == B.FP64 else mixed_tol(b))
+
+
+def test_full_genz_singular_covariance_is_not_pd(ctx):
+    """Sites 0 and 1 equal, no nugget: the second pivot is exactly 0."""
+    s, u, cov = _ordered(40, 12)
+    s[1] = s[0]
+    with pytest.raises(O.OracleError):
+        O.full_genz(s, cov, u, 256, 4, 0)
+    with pytest.raises(B.VecchiaError) as e:
+        B.vecchia_full_genz(ctx, s, cov, u, 256, 4, precision=B.FP64)
+    assert e.value.status == B.ERR_NOT_PD and B.vecchia_last_error_site(ctx) == 1
