@@ -99,8 +99,9 @@ int vecchia_set_stream(vecchia_ctx* ctx, void* cuda_stream);
  * host (MAXMIN: O(D^2) integer work over the host's cores).  With a context,
  * MAXMIN runs on the device (one persistent CTA: a tournament tree over the
  * distances to the chosen set, each pick scanning only the grid cells within
- * the current maximum distance), with the same result; XY and IDENTITY stay
- * on the host.  MAXMIN: first the site nearest the centre of the quantised
+ * the current maximum distance), with the same result; XY with both arrays
+ * on the device and D <= 8192 runs on the device (each site's rank by
+ * counting the smaller keys); the other cases run on the host.  MAXMIN: first the site nearest the centre of the quantised
  * bounding box, then repeatedly the site farthest from the chosen ones, on
  * quantised coordinates, ties to the smaller index. */
 int vecchia_order(vecchia_ctx* ctx, const double* sites, int64_t D, int kind, int32_t* perm);

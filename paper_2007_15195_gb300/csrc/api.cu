@@ -279,26 +279,32 @@ uint32_t* lattice_for(vecchia_ctx* c, int64_t N) {
     return d;
 }
 
-// Built-in tile: 4 warps; two points per lane for blocks of up to 21 variables
-// (registers allow the second independent chain there), one above; enough
-// shift groups (a power of two, so S = 2^k splits evenly) for ~4096 CTA items,
-// but never fewer shifts per item than warps (a warp without a unit idles).
-// Blocks above 32 variables: 8 warps and every shift in one item, so the
-// one-warp Cholesky of up to 64 variables is shared by the most work.
+// Built-in tile (measured on the 50x50 grid): mixed blocks of up to 32
+// variables run two points per lane (one vote per step for both), 4 warps up
+// to 21 variables and 8 above; FP64 one point, 4 warps.  Shift groups (a power
+// of two, so S = 2^k splits evenly) until a launch has ~2048 CTA items, never
+// fewer shifts per item than warps (a warp without a unit idles); ~4096 items
+// for blocks of up to 16 variables, which fit more CTAs per SM.  Blocks
+// above 32 variables: 8 warps, one point per lane, every shift of a term in
+// one item, so the one-warp Cholesky of up to 64 variables is shared by the
+// most work.
 GenzTile default_tile(bool mixed, int64_t total_sites, int max_S, int bucket) {
     GenzTile t;
-    if (vk::kDmaxBuckets[bucket] > 32) {
+    const int dmax = vk::kDmaxBuckets[bucket];
+    if (dmax > 32) {
         t.warps = 8;
         t.points = 1;
         t.slices = 1;
         t.groups = 1;
         return t;
     }
-    t.warps = 4;
-    t.points = (mixed && vk::kDmaxBuckets[bucket] <= 21) ? 2 : 1;
+    t.warps = (mixed && dmax > 21) ? 8 : 4;
+    t.points = mixed ? 2 : 1;
     t.slices = 1;
+    // small blocks fit more CTAs per SM: they want more items
+    const int64_t target = dmax <= 16 ? 4096 : 2048;
     int g = 1;
-    while (g < max_S && (int64_t)g * total_sites < 4096 && max_S / (2 * g) >= t.warps) g *= 2;
+    while (g < max_S && (int64_t)g * total_sites < target && max_S / (2 * g) >= t.warps) g *= 2;
     t.groups = g;
     return t;
 }
@@ -929,6 +935,15 @@ int vecchia_order(vecchia_ctx* c, const double* sites, int64_t D, int kind, int3
     // with no context both arrays are host memory and the ordering runs on the host
     const bool dev_in = c && is_device_ptr(sites), dev_out = c && is_device_ptr(perm);
     if (c && (dev_in || dev_out) && cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    if (c && kind == VECCHIA_ORDER_XY && dev_in && dev_out && D <= vk::kOrderXyDeviceMax) {
+        // XY on the device: each site's rank counts the smaller (x, y, index) keys
+        const cudaError_t e = vk::launch_order_xy(sites, D, perm, c->stream);
+        if (e != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return VECCHIA_ERR_CUDA;
+        }
+        return VECCHIA_OK;
+    }
     if (c && kind == VECCHIA_ORDER_MAXMIN) {  // exact maxmin on the device
         if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
         Carve dv(nullptr);

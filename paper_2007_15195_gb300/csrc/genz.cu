@@ -275,6 +275,23 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
     const float4 c = sc[t];
     const float lz = c.x;
     const uint32_t G = __float_as_uint(c.y), Dt = __float_as_uint(c.z);
+    if constexpr (P == 1) {  // one point per lane: the per-point form keeps fewer values live
+        if (!FIRST) g[0] = __fmul_rn(g[0], e[0]);
+        const uint32_t X = kk[0] * G + Dt;
+        const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
+        const float w = __fmul_rn(__uint2float_rn(V), 0x1p-31f);
+        const float yv = special::phiinv_pq(__fmul_rn(w, e[0]), fmaf(w, ec[0], __fsub_rn(1.0f, w)));
+        const float z = fmaf(-lz, yv, R[0][0]);
+#pragma unroll
+        for (int r = 0; r < W; ++r) R[0][r] = fmaf(-lup[r], yv, R[0][r + 1]);
+        special::phi_pair_fast(z, e[0], ec[0]);
+        return;
+    }
+    // Phi^{-1} of every point's w_t e_t first, so one full-warp vote decides
+    // the tail pieces for all of them (every lane of the warp runs this step)
+    float pp[P], qq[P], y[P];
+    bool tail[P];
+    bool any_tail = false;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         if (!FIRST) g[p] = __fmul_rn(g[p], e[p]);  // g = e_1 ... e_t
@@ -282,10 +299,21 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
         const uint32_t X = kk[p] * G + Dt;
         const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
         const float w = __fmul_rn(__uint2float_rn(V), 0x1p-31f);
-        const float y = special::phiinv_pq(__fmul_rn(w, e[p]), fmaf(w, ec[p], __fsub_rn(1.0f, w)));
-        const float z = fmaf(-lz, y, R[p][0]);
+        pp[p] = __fmul_rn(w, e[p]);
+        qq[p] = fmaf(w, ec[p], __fsub_rn(1.0f, w));
+        y[p] = special::phiinv_central(pp[p], qq[p], tail[p]);
+        any_tail = any_tail || tail[p];
+    }
+    if (__any_sync(0xffffffffu, any_tail)) {
 #pragma unroll
-        for (int r = 0; r < W; ++r) R[p][r] = fmaf(-lup[r], y, R[p][r + 1]);
+        for (int p = 0; p < P; ++p) y[p] = special::phiinv_with_tail(pp[p], qq[p], tail[p], y[p]);
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const float yv = special::phiinv_finish(pp[p], qq[p], y[p]);
+        const float z = fmaf(-lz, yv, R[p][0]);
+#pragma unroll
+        for (int r = 0; r < W; ++r) R[p][r] = fmaf(-lup[r], yv, R[p][r + 1]);
         special::phi_pair_fast(z, e[p], ec[p]);
     }
 }

@@ -812,6 +812,50 @@ cudaError_t launch_maxmin(const double* sites, int64_t D, int32_t* perm, void* s
     return cudaGetLastError();
 }
 
+// ---- XY ordering on the device (D <= 8192) ----------------------------------
+// The rank of site i in the (x, y, index) order is the number of sites whose
+// key is smaller (exact double comparisons, the host's XY rule; keys are
+// unique through the index); perm[rank_i] = i.  One thread per site, the
+// other sites streamed through shared memory in tiles.
+
+constexpr int kXyMax = 8192;
+constexpr int kXyThreads = 256;
+
+// Order-preserving integer image of a double (-0 taken as +0, as the
+// comparison x < y treats them): integer compares instead of FP64 ones.
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x == 0.0 ? 0.0 : x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+__global__ void __launch_bounds__(kXyThreads) order_xy_kernel(const double* __restrict__ sites, int D,
+                                                              int32_t* __restrict__ perm) {
+    __shared__ unsigned long long tx[kXyThreads], ty[kXyThreads];
+    const int i = blockIdx.x * kXyThreads + threadIdx.x;
+    const bool valid = i < D;
+    const unsigned long long xi = valid ? ord_key(sites[2 * i]) : 0ULL, yi = valid ? ord_key(sites[2 * i + 1]) : 0ULL;
+    int rank = 0;
+    for (int j0 = 0; j0 < D; j0 += kXyThreads) {
+        const int j = j0 + threadIdx.x;
+        __syncthreads();
+        tx[threadIdx.x] = j < D ? ord_key(sites[2 * j]) : 0ULL;
+        ty[threadIdx.x] = j < D ? ord_key(sites[2 * j + 1]) : 0ULL;
+        __syncthreads();
+        const int n = min(kXyThreads, D - j0);
+        for (int t = 0; t < n; ++t) {
+            const unsigned long long xj = tx[t], yj = ty[t];
+            rank += (xj < xi) || (xj == xi && (yj < yi || (yj == yi && j0 + t < i)));
+        }
+    }
+    if (valid) perm[rank] = i;
+}
+
+cudaError_t launch_order_xy(const double* sites, int64_t D, int32_t* perm, cudaStream_t st) {
+    if (D <= 0 || D > kXyMax) return cudaErrorInvalidValue;
+    order_xy_kernel<<<(unsigned)((D + kXyThreads - 1) / kXyThreads), kXyThreads, 0, st>>>(sites, (int)D, perm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_group_union(const int32_t* per_site, int64_t D, int m, int p, int cmax, int32_t* cond,
                                int32_t* count, int* overflow, cudaStream_t st) {
     const int64_t G = (D + p - 1) / p;

@@ -94,14 +94,19 @@ extern "C" int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const doub
     const bool mixed = precision == VECCHIA_MIXED;
     constexpr int kDim = vk::kMaxDim;
 
-    // tile: the built-in rule of vecchia_log_cdf (4 warps; two points per lane
-    // for blocks of up to 21 variables; power-of-two shift groups for ~4096 CTA
-    // items, never fewer shifts per item than warps)
+    // tile: the built-in rule of vecchia_log_cdf (mixed: two points per lane up
+    // to 32 variables, 8 warps above 21; power-of-two shift groups for ~2048
+    // CTA items (4096 up to 16 variables), never fewer shifts per item than
+    // warps; above 32 variables 8
+    // warps, one point, one group)
     const int bucket = vk::bucket_of(m + 1);
+    const int dmax = vk::kDmaxBuckets[bucket];
+    const int warps = (mixed && dmax > 21) ? 8 : 4;
     int groups = 1;
-    while (groups < S && (int64_t)groups * D < 4096 && S / (2 * groups) >= 4) groups *= 2;
-    vk::GenzTile tile{4, (mixed && vk::kDmaxBuckets[bucket] <= 21) ? 2 : 1, 1, groups};
-    if (vk::kDmaxBuckets[bucket] > 32) tile = vk::GenzTile{8, 1, 1, 1};
+    const int64_t target = dmax <= 16 ? 4096 : 2048;
+    while (groups < S && (int64_t)groups * D < target && S / (2 * groups) >= warps) groups *= 2;
+    vk::GenzTile tile{warps, mixed ? 2 : 1, 1, groups};
+    if (dmax > 32) tile = vk::GenzTile{8, 1, 1, 1};
 
     // scratch layout (every offset a multiple of 256 bytes)
     size_t off = 0;

@@ -129,6 +129,23 @@ __device__ __forceinline__ float phiinv_pq(float p, float q) {
     return __fmul_rn(__fsub_rn(p, q), f);
 }
 
+// The same quantile in three parts for callers that vote once for several
+// values: the central factor f (and whether the tail pieces are needed), the
+// tail factor where needed, and (p - q) f.  Same arithmetic as phiinv_pq.
+__device__ __forceinline__ float phiinv_central(float p, float q, bool& tail) {
+    const float L = lg2(__fmul_rn(p, q));
+    tail = !(L > kINV1Lmin);
+    return horner(kINV1C, fmaf(L, kINV1LA, kINV1LB));
+}
+__device__ __forceinline__ float phiinv_with_tail(float p, float q, bool tail, float f) {
+    const float L = lg2(__fmul_rn(p, q));
+    const float ft = finv_tail(__fmul_rn(-kLn2, __fadd_rn(L, 2.0f)));
+    return tail ? ft : f;
+}
+__device__ __forceinline__ float phiinv_finish(float p, float q, float f) {
+    return __fmul_rn(__fsub_rn(p, q), f);
+}
+
 // Phi^{-1}(r) for r = 2^lr2 < 2^-64 (log2 input).
 __device__ __forceinline__ float phiinv_log2(float lr2) {
     const float w = -fmaf(kLn2, fmaxf(lr2, -1009.0f), kLn4);

@@ -238,3 +238,18 @@ def test_full_genz_singular_covariance_is_not_pd(ctx):
     with pytest.raises(B.VecchiaError) as e:
         B.vecchia_full_genz(ctx, s, cov, u, 256, 4, precision=B.FP64)
     assert e.value.status == B.ERR_NOT_PD and B.vecchia_last_error_site(ctx) == 1
+
+
+@pytest.mark.parametrize("D,kind", [(1, "u"), (3, "u"), (2500, "grid"), (5000, "u"), (8192, "u"), (8193, "u"),
+                                    (999, "dup")])
+def test_device_xy_order_equals_oracle(ctx, D, kind):
+    import torch
+    if kind == "grid":
+        s = inputs.grid_sites(50)[::-1].copy()  # many equal x: y and then the index decide
+    elif kind == "dup":
+        s = np.repeat(inputs.uniform_sites(D // 3, 5), 3, axis=0)
+    else:
+        s = inputs.uniform_sites(D, D)
+    ref = O.order(s, O.ORDER_XY)
+    got = B.vecchia_order(ctx, torch.from_numpy(s).cuda(), "xy")
+    assert np.array_equal(got.cpu().numpy(), ref)
