@@ -63,6 +63,10 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 ALG_OPS_STEP = 34
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the Genz kernel on the headline workload (m = 20, built-in tile:
+# genz_kernel<21, 2, fast>), from one ncu capture of that launch.
+GENZ_TRAFFIC_BYTES_M20 = 359_168
 
 
 def parse():
@@ -226,7 +230,10 @@ def run_ours(args):
         lp, se = V.vecchia_log_cdf(ctx, s_ord, nbr, m, prob.cov, u_ord, N, S, seed, precision)
         return lp, se
 
-    launches_per_step = {V.MIXED: 11, V.FP64: 10}
+    # library kernels per step: XY ranks + scatter, gather, neighbour grid (bbox,
+    # quantize, scan, scatter) + search, init, shifts, Genz, re-evaluation
+    # (mixed only), log-sum partial + final
+    launches_per_step = {V.MIXED: 14, V.FP64: 13}
 
     def timed(n_steps, precision, seed0):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -306,7 +313,8 @@ def run_ours(args):
                       "p99_ms": float(np.percentile(ms64, 99)),
                       "genz_kernel_ms": float(np.mean(genz64))} if len(ms64) else None),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": GENZ_TRAFFIC_BYTES_M20 if m == 20 else None,
                          "kernel": "genz_kernel (mixed)", "kernel_ms": genz_s * 1000.0,
                          "ops": "FP32-pipe lane operations, an FMA counting once; %d per Genz step "
                                 "+ q(q+1)/2 FMAs per point; peak = %d SMs x %d lanes x %.0f MHz"

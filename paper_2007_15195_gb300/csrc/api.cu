@@ -937,7 +937,9 @@ int vecchia_order(vecchia_ctx* c, const double* sites, int64_t D, int kind, int3
     if (c && (dev_in || dev_out) && cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
     if (c && kind == VECCHIA_ORDER_XY && dev_in && dev_out && D <= vk::kOrderXyDeviceMax) {
         // XY on the device: each site's rank counts the smaller (x, y, index) keys
-        const cudaError_t e = vk::launch_order_xy(sites, D, perm, c->stream);
+        int st = ensure_arena(c, vk::order_xy_scratch_bytes(D));
+        if (st != VECCHIA_OK) return st;
+        const cudaError_t e = vk::launch_order_xy(sites, D, perm, c->arena, c->stream);
         if (e != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
             cudaGetLastError();
             return VECCHIA_ERR_CUDA;

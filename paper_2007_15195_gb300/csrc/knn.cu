@@ -814,9 +814,8 @@ cudaError_t launch_maxmin(const double* sites, int64_t D, int32_t* perm, void* s
 
 // ---- XY ordering on the device (D <= 8192) ----------------------------------
 // The rank of site i in the (x, y, index) order is the number of sites whose
-// key is smaller (exact double comparisons, the host's XY rule; keys are
-// unique through the index); perm[rank_i] = i.  One thread per site, the
-// other sites streamed through shared memory in tiles.
+// key is smaller (the host's XY rule; keys are unique through the index);
+// perm[rank_i] = i.
 
 constexpr int kXyMax = 8192;
 constexpr int kXyThreads = 256;
@@ -828,31 +827,47 @@ __device__ __forceinline__ unsigned long long ord_key(double x) {
     return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
 }
 
-__global__ void __launch_bounds__(kXyThreads) order_xy_kernel(const double* __restrict__ sites, int D,
-                                                              int32_t* __restrict__ perm) {
-    __shared__ unsigned long long tx[kXyThreads], ty[kXyThreads];
+// Grid (site blocks x chunks of the other sites): each thread counts, for its
+// site, the smaller keys of one chunk and adds the count to rank[i] (integer
+// adds: the total does not depend on their order).
+constexpr int kXyChunk = 512;
+
+__global__ void __launch_bounds__(kXyThreads) order_xy_rank_kernel(const double* __restrict__ sites, int D,
+                                                                   int* __restrict__ rank) {
+    __shared__ unsigned long long tx[kXyChunk], ty[kXyChunk];
     const int i = blockIdx.x * kXyThreads + threadIdx.x;
-    const bool valid = i < D;
-    const unsigned long long xi = valid ? ord_key(sites[2 * i]) : 0ULL, yi = valid ? ord_key(sites[2 * i + 1]) : 0ULL;
-    int rank = 0;
-    for (int j0 = 0; j0 < D; j0 += kXyThreads) {
-        const int j = j0 + threadIdx.x;
-        __syncthreads();
-        tx[threadIdx.x] = j < D ? ord_key(sites[2 * j]) : 0ULL;
-        ty[threadIdx.x] = j < D ? ord_key(sites[2 * j + 1]) : 0ULL;
-        __syncthreads();
-        const int n = min(kXyThreads, D - j0);
-        for (int t = 0; t < n; ++t) {
-            const unsigned long long xj = tx[t], yj = ty[t];
-            rank += (xj < xi) || (xj == xi && (yj < yi || (yj == yi && j0 + t < i)));
-        }
+    const int j0 = blockIdx.y * kXyChunk;
+    const int n = min(kXyChunk, D - j0);
+    for (int t = threadIdx.x; t < n; t += kXyThreads) {
+        tx[t] = ord_key(sites[2 * (j0 + t)]);
+        ty[t] = ord_key(sites[2 * (j0 + t) + 1]);
     }
-    if (valid) perm[rank] = i;
+    __syncthreads();
+    if (i >= D) return;
+    const unsigned long long xi = ord_key(sites[2 * i]), yi = ord_key(sites[2 * i + 1]);
+    int cnt = 0;
+    for (int t = 0; t < n; ++t) {
+        const unsigned long long xj = tx[t], yj = ty[t];
+        cnt += (xj < xi) || (xj == xi && (yj < yi || (yj == yi && j0 + t < i)));
+    }
+    if (cnt) atomicAdd(&rank[i], cnt);
 }
 
-cudaError_t launch_order_xy(const double* sites, int64_t D, int32_t* perm, cudaStream_t st) {
+__global__ void order_xy_scatter_kernel(const int* __restrict__ rank, int D, int32_t* __restrict__ perm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < D) perm[rank[i]] = i;
+}
+
+size_t order_xy_scratch_bytes(int64_t D) { return sizeof(int) * (size_t)(D > 0 ? D : 1); }
+
+cudaError_t launch_order_xy(const double* sites, int64_t D, int32_t* perm, void* scratch, cudaStream_t st) {
     if (D <= 0 || D > kXyMax) return cudaErrorInvalidValue;
-    order_xy_kernel<<<(unsigned)((D + kXyThreads - 1) / kXyThreads), kXyThreads, 0, st>>>(sites, (int)D, perm);
+    int* rank = (int*)scratch;
+    cudaError_t e = cudaMemsetAsync(rank, 0, sizeof(int) * (size_t)D, st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((D + kXyThreads - 1) / kXyThreads), (unsigned)((D + kXyChunk - 1) / kXyChunk));
+    order_xy_rank_kernel<<<grid, kXyThreads, 0, st>>>(sites, (int)D, rank);
+    order_xy_scatter_kernel<<<(unsigned)((D + 255) / 256), 256, 0, st>>>(rank, (int)D, perm);
     return cudaGetLastError();
 }
 

@@ -116,7 +116,8 @@ cudaError_t launch_knn(const double* sites, int64_t D, int m, int32_t* nbr, void
 size_t maxmin_scratch_bytes(int64_t D);
 cudaError_t launch_maxmin(const double* sites, int64_t D, int32_t* perm, void* scratch, cudaStream_t st);
 // XY ordering (x, then y, then index) of D <= 8192 device sites (ranks by counting).
-cudaError_t launch_order_xy(const double* sites, int64_t D, int32_t* perm, cudaStream_t st);
+size_t order_xy_scratch_bytes(int64_t D);
+cudaError_t launch_order_xy(const double* sites, int64_t D, int32_t* perm, void* scratch, cudaStream_t st);
 constexpr int64_t kOrderXyDeviceMax = 8192;
 // Union of the members' sets (per_site: D x m from launch_knn with group p)
 // into ascending rows of cond (n_groups x cmax, -1 padded) and count; *overflow
