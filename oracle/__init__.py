@@ -463,3 +463,64 @@ def mixture_log_cdf(sites, nbr, m, cov, x, N, S, seed, beta, gamma, n_nodes):
     terms = np.array(terms)
     mx = terms.max()
     return float(mx + np.log(np.sum(np.exp(terms - mx))))
+
+
+# ---- censored likelihood G_I (Sec. 4, Eq. model05) ---------------------------
+def vecchia_from_matrix(Sigma, nbr, m, u, N, S, seed, return_terms=False):
+    """Eq. (vecchia-cdf) for N(0, Sigma) with Sigma given as a matrix: term i
+    is the block (N_i ascending, i) of Sigma, by genz_sums on the lattice and
+    shifts of dimension max(m, 1); reduced as vecchia_reduce."""
+    Sigma = _f64(Sigma)
+    u = _f64(u)
+    D = Sigma.shape[0]
+    dim = max(m, 1)
+    g, dl = lattice(N, dim), shifts(seed, S, dim)
+    num = np.zeros((D, S))
+    den = np.zeros((D, S))
+    for i in range(D):
+        q = min(m, i)
+        b = [int(j) for j in nbr[i, :q]] + [i]
+        num[i], den[i] = genz_sums(Sigma[np.ix_(b, b)], u[b], N, S, g, dl)
+    lp, se, terms = vecchia_reduce(num, den)
+    return (lp, se, terms) if return_terms else (lp, se)
+
+
+def censored_log_cdf(sites_c, nbr, m, sites_i, cov, x_c, x_i, N, S, seed, beta=0.5, gamma=1.0, n_nodes=16):
+    """log G_I(x) of Eq. (model05): the observations x_I above the threshold
+    enter through their density, the censored ones x_c through the CDF of
+    their conditional law given x_I:
+        G_I = int Phi_c{(x_c - mu)/r; Sigma_{c|I}} phi_k(x_I/r; Sigma_II) r^-k dF_R(r),
+        mu = Sigma_cI Sigma_II^-1 x_I,  Sigma_{c|I} = Sigma_cc - Sigma_cI Sigma_II^-1 Sigma_Ic,
+    with Phi_c by Eq. (vecchia-cdf) on the censored sites (ordered; rows nbr),
+    Phi_c(y/r; A) = Phi_c(y; r^2 A), phi_k in closed form, and the integral by
+    the rule of mixture_nodes; n_nodes = 0 means R = 1 (the Gaussian case).
+    Linear algebra by numpy's LAPACK solves."""
+    sc = _f64(sites_c).reshape(-1, 2)
+    si = _f64(sites_i).reshape(-1, 2)
+    xc, xi = _f64(x_c), _f64(x_i)
+    c, k = sc.shape[0], si.shape[0]
+    Sig = cov_matrix_t(np.concatenate([si, sc]), cov)
+    Sii, Sic, Scc = Sig[:k, :k], Sig[:k, k:], Sig[k:, k:]
+    if k:
+        Scond = Scc - Sic.T @ np.linalg.solve(Sii, Sic)
+        sol = np.linalg.solve(Sii, xi)
+        mu = Sic.T @ sol
+        quad = float(xi @ sol)
+        logdet = float(np.linalg.slogdet(Sii)[1])
+    else:
+        Scond, mu, quad, logdet = Scc, np.zeros(c), 0.0, 0.0
+
+    def node(r):
+        lp = 0.0
+        if c:
+            lp, _ = vecchia_from_matrix(r * r * Scond, nbr, m, xc - mu, N, S, seed)
+        # log phi_k(x_I / r; Sigma_II) - k log r
+        ld = -0.5 * k * np.log(2 * np.pi) - 0.5 * logdet - quad / (2 * r * r) - k * np.log(r)
+        return lp + ld
+
+    if n_nodes == 0:
+        return float(node(1.0))
+    v, w = mixture_nodes(n_nodes)
+    terms = np.array([np.log(wq) + node(float(mixing_quantile(vq, beta, gamma))) for vq, wq in zip(v, w)])
+    mx = terms.max()
+    return float(mx + np.log(np.sum(np.exp(terms - mx))))
