@@ -307,6 +307,28 @@ int vecchia_full_genz(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, 
                       const double* u, int64_t N, int S, uint64_t seed, int precision, double* log_p,
                       double* rel_se);
 
+/* The censored likelihood G_I of Sec. 4 (Eq. model05) for one replicate:
+ * the nc censored values (sites_c ordered, x_c, neighbour rows nbr nc x m
+ * among them) are below the threshold, the ni observed ones (sites_i, x_i)
+ * above it.  With Sigma_II = L L^T over the observed sites,
+ *   G_I = int Phi_nc{(x_c - mu)/r; Sigma_{c|I}} phi_ni(x_I / r; Sigma_II) r^-ni dF_R(r),
+ *   mu = Sigma_cI Sigma_II^-1 x_I,  Sigma_{c|I} = Sigma_cc - Sigma_cI Sigma_II^-1 Sigma_Ic,
+ * Phi_nc by Eq. (vecchia-cdf) on the censored sites with the conditional
+ * covariance (each block entry minus V_a . V_b, V = L^-1 Sigma_Ic, on the
+ * device), phi in closed form, and the integral by the rule of
+ * vecchia_mixture_log_cdf (n_nodes >= 1; beta, gamma of Eq. model02);
+ * n_nodes = 0 takes R = 1, the Gaussian censored likelihood.  ni = 0 is
+ * vecchia_mixture_log_cdf (or vecchia_log_cdf); nc = 0 the density alone.
+ * Arrays host or device, all of one kind; 1 <= nc + ni, ni <=
+ * VECCHIA_CENSOR_MAX_OBS.  A non-positive pivot of Sigma_II gives
+ * VECCHIA_ERR_NOT_PD with the observed site's index in
+ * vecchia_last_error_site(). */
+#define VECCHIA_CENSOR_MAX_OBS 4096
+int vecchia_censored_log_cdf(vecchia_ctx* ctx, const double* sites_c, int64_t nc, const int32_t* nbr, int m,
+                             const double* sites_i, int64_t ni, vecchia_cov cov, const double* x_c,
+                             const double* x_i, int64_t N, int S, uint64_t seed, double beta, double gamma,
+                             int n_nodes, int precision, double* log_g, double* std_err);
+
 /* Korobov generating vector g[j] = a^j mod N, j < dim (host array): a in
  * [2, N/2], gcd(a, N) = 1, minimising the weighted P2 criterion over 30
  * dimensions with weights 1/j^2 (ties: smaller a).  N < 4 gives a = 1. */

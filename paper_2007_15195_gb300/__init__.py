@@ -9,7 +9,8 @@ call does, and fails if it has not been built.
 """
 from .binding import (COND_NEAREST, COND_RANDOM, COV_ANISO_EXP, COV_EXPONENTIAL, COV_MATERN, FP64, MIXED,
                       ORDER_IDENTITY, ORDER_MAXMIN, ORDER_XY, Context, Plan, VecchiaError, make_cov,
-                      vecchia_create, vecchia_destroy, vecchia_apply_order, vecchia_full_genz, vecchia_genz_time_ms,
+                      vecchia_censored_log_cdf, vecchia_create, vecchia_destroy, vecchia_apply_order, vecchia_full_genz,
+                      vecchia_genz_time_ms,
                       vecchia_group_conditioning, vecchia_grouped_log_cdf, vecchia_last_error_site,
                       vecchia_lattice, vecchia_log_cdf, vecchia_log_cdf_batch, vecchia_log_cdf_terms,
                       vecchia_mixture_log_cdf, vecchia_neighbors, vecchia_order, vecchia_plan_create,
@@ -18,7 +19,7 @@ from .binding import (COND_NEAREST, COND_RANDOM, COV_ANISO_EXP, COV_EXPONENTIAL,
 __all__ = [
     "COND_NEAREST", "COND_RANDOM", "COV_ANISO_EXP", "COV_EXPONENTIAL", "COV_MATERN", "FP64", "MIXED",
     "ORDER_IDENTITY", "ORDER_MAXMIN", "ORDER_XY", "Context", "Plan", "VecchiaError", "vecchia_plan_create",
-    "make_cov", "vecchia_create", "vecchia_destroy", "vecchia_apply_order", "vecchia_full_genz",
+    "make_cov", "vecchia_censored_log_cdf", "vecchia_create", "vecchia_destroy", "vecchia_apply_order", "vecchia_full_genz",
     "vecchia_genz_time_ms",
     "vecchia_group_conditioning", "vecchia_grouped_log_cdf", "vecchia_last_error_site", "vecchia_lattice",
     "vecchia_log_cdf", "vecchia_log_cdf_batch", "vecchia_log_cdf_terms", "vecchia_mixture_log_cdf",

@@ -109,6 +109,9 @@ def lib():
                                               C.POINTER(C.c_double)]
         L.vecchia_full_genz.argtypes = [_vp, _vp, C.c_int64, vecchia_cov, _vp, C.c_int64, C.c_int, C.c_uint64,
                                         C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.vecchia_censored_log_cdf.argtypes = [_vp, _vp, C.c_int64, _vp, C.c_int, _vp, C.c_int64, vecchia_cov, _vp,
+                                               _vp, C.c_int64, C.c_int, C.c_uint64, C.c_double, C.c_double,
+                                               C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.vecchia_lattice.argtypes = [C.c_int64, C.c_int, _vp]
         L.vecchia_shifts.argtypes = [C.c_uint64, C.c_int, C.c_int, _vp]
         L.vecchia_last_error_site.restype = C.c_int64
@@ -315,6 +318,23 @@ def vecchia_full_genz(ctx, sites_ordered, cov, u, N, S, seed=0, precision=MIXED)
                                    C.c_uint64(int(seed)), int(precision), C.byref(lp), C.byref(se)),
            "vecchia_full_genz", ctx)
     return lp.value, se.value
+
+
+def vecchia_censored_log_cdf(ctx, sites_c, nbr, m, sites_i, cov, x_c, x_i, N, S, seed=0, beta=0.5, gamma=1.0,
+                             n_nodes=16, precision=MIXED):
+    """Censored likelihood log G_I (censored sites_c/x_c with neighbour rows nbr,
+    observed sites_i/x_i); n_nodes = 0 for R = 1.  Returns (log_g, std_err)."""
+    sc, xc = _f64(sites_c), _f64(x_c)
+    si, xi = _f64(sites_i), _f64(x_i)
+    nc, ni = int(sc.shape[0]), int(si.shape[0])
+    nb = _i32(nbr) if (m > 0 and nc > 0) else None
+    lg, se = C.c_double(), C.c_double()
+    _check(lib().vecchia_censored_log_cdf(ctx.handle, _ptr(sc) if nc else None, nc, _ptr(nb), int(m),
+                                          _ptr(si) if ni else None, ni, make_cov(cov), _ptr(xc) if nc else None,
+                                          _ptr(xi) if ni else None, int(N), int(S), C.c_uint64(int(seed)),
+                                          float(beta), float(gamma), int(n_nodes), int(precision), C.byref(lg),
+                                          C.byref(se)), "vecchia_censored_log_cdf", ctx)
+    return lg.value, se.value
 
 
 def vecchia_mixture_log_cdf(ctx, sites_ordered, nbr, m, cov, x, N, S, seed=0, beta=0.5, gamma=1.0,

@@ -19,6 +19,8 @@ struct vecchia_ctx {
     size_t arena_cap = 0;
     void* host_stage = nullptr;  // pinned
     size_t host_stage_cap = 0;
+    void* aux = nullptr;  // device buffer for inputs derived before a batch (kept apart from the arena)
+    size_t aux_cap = 0;
     std::map<int64_t, uint32_t*> lattice_dev;  // N -> device [g(32) | gfix(32)]
     int64_t last_error_site = -1;
     vk::GenzTile tile[2][vk::kNumBuckets];
@@ -84,6 +86,22 @@ int ensure_arena(vecchia_ctx* c, size_t bytes) {
         return VECCHIA_ERR_NOMEM;
     }
     c->arena_cap = cap;
+    return VECCHIA_OK;
+}
+
+int ensure_aux(vecchia_ctx* c, size_t bytes) {
+    if (bytes <= c->aux_cap) return VECCHIA_OK;
+    if (c->aux) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->aux);
+        c->aux = nullptr;
+        c->aux_cap = 0;
+    }
+    if (cudaMalloc(&c->aux, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_NOMEM;
+    }
+    c->aux_cap = bytes;
     return VECCHIA_OK;
 }
 
@@ -589,9 +607,11 @@ void collect(const Batch& B, const char* H, double* log_p, double* std_err, int3
     }
 }
 
+// lr_V, lr_k, lr_scale (one per problem): a low-rank correction of every
+// problem's covariance (device V, nc x lr_k), for conditional laws.
 int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precision,
                  double* log_p, double* std_err, int32_t* status, double* terms, double* num,
-                 double* den) {
+                 double* den, const double* lr_V = nullptr, int lr_k = 0, const double* lr_scale = nullptr) {
     if (!c || !probs || n < 1 || !log_p || !std_err || !status) return VECCHIA_ERR_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
     c->last_error_site = -1;
@@ -613,6 +633,14 @@ int run_problems(vecchia_ctx* c, const vecchia_problem* probs, int n, int precis
     char* A = (char*)c->arena;
     char* H = (char*)c->host_stage;
     fill_blob(B, A, H, terms);
+    if (lr_k > 0) {
+        ProbDev* hp = (ProbDev*)(H + B.b_probs);
+        for (int i = 0; i < n; ++i) {
+            hp[i].lr_V = lr_V;
+            hp[i].lr_k = lr_k;
+            hp[i].lr_scale = lr_scale[i];
+        }
+    }
     const cudaStream_t s = c->stream;
     cudaError_t e = stage_inputs(B, A, s);
     if (e == cudaSuccess) e = enqueue(B, A, H, s, terms != nullptr, c);
@@ -758,6 +786,21 @@ double mixing_radius(double L, double beta, double gamma) {
     return std::exp(L / gamma);
 }
 
+// Nodes r_q and weights w_q of int_0^inf h(r) dF_R(r) = int_0^1 h(F_R^{-1}(v)) dv.
+// F_R^{-1} is singular at v = 1, so v = 1 - (1 - t)^4 (dv = 4 (1 - t)^3 dt)
+// flattens the integrand there before the Gauss-Legendre rule in t:
+// L = -log(1 - v) = -4 log(1 - t).
+void mixture_nodes(int n, double beta, double gamma, std::vector<double>& r, std::vector<double>& w) {
+    std::vector<double> t;
+    gauss_legendre01(n, t, w);
+    r.assign(n, 0.0);
+    for (int q = 0; q < n; ++q) {
+        const double omt = 1.0 - t[q];
+        w[q] *= 4.0 * omt * omt * omt;
+        r[q] = mixing_radius(-4.0 * std::log1p(-t[q]), beta, gamma);
+    }
+}
+
 // ------------------------------ host ordering ------------------------------
 
 void quantize_host(const double* s, int64_t D, std::vector<int64_t>& q) {
@@ -889,6 +932,7 @@ int vecchia_destroy(vecchia_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     if (c->arena) cudaFree(c->arena);
+    if (c->aux) cudaFree(c->aux);
     if (c->host_stage) cudaFreeHost(c->host_stage);
     for (auto& kv : c->lattice_dev) cudaFree(kv.second);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1293,16 +1337,11 @@ int vecchia_mixture_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, cons
         return VECCHIA_ERR_ARG;
     *log_g = NAN;
     *std_err = NAN;
-    // G = int_0^1 Phi_D(x / F_R^{-1}(v)) dv.  F_R^{-1} is singular at v = 1,
-    // so v = 1 - (1 - t)^4 (dv = 4 (1 - t)^3 dt) flattens the integrand there
-    // before the Gauss-Legendre rule in t: L = -log(1 - v) = -4 log(1 - t).
-    std::vector<double> t, w;
-    gauss_legendre01(n_nodes, t, w);
+    std::vector<double> rq, w;
+    mixture_nodes(n_nodes, beta, gamma, rq, w);
     std::vector<vecchia_problem> probs(n_nodes);
     for (int q = 0; q < n_nodes; ++q) {
-        const double omt = 1.0 - t[q];
-        w[q] *= 4.0 * omt * omt * omt;
-        const double r = mixing_radius(-4.0 * std::log1p(-t[q]), beta, gamma);
+        const double r = rq[q];
         vecchia_problem& p = probs[q];
         p.sites = sites;
         p.nbr = nbr;
@@ -1333,6 +1372,155 @@ int vecchia_mixture_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, cons
     double seb = 0.0;
     for (int q = 0; q < n_nodes; ++q) seb += std::exp(std::log(w[q]) + lp[q] - *log_g) * se[q];
     *std_err = seb;
+    return VECCHIA_OK;
+}
+
+int vecchia_censored_log_cdf(vecchia_ctx* c, const double* sites_c, int64_t nc, const int32_t* nbr, int m,
+                             const double* sites_i, int64_t ni, vecchia_cov cov, const double* x_c,
+                             const double* x_i, int64_t N, int S, uint64_t seed, double beta, double gamma,
+                             int n_nodes, int precision, double* log_g, double* std_err) {
+    if (!c || !log_g || !std_err || nc < 0 || ni < 0 || nc + ni < 1) return VECCHIA_ERR_ARG;
+    if ((nc > 0 && (!sites_c || !x_c || (m > 0 && !nbr))) || (ni > 0 && (!sites_i || !x_i))) return VECCHIA_ERR_ARG;
+    if (n_nodes < 0 || n_nodes > 256 || m < 0) return VECCHIA_ERR_ARG;
+    if (n_nodes > 0 && (!(beta >= 0.0) || !(gamma > 0.0) || !std::isfinite(beta) || !std::isfinite(gamma)))
+        return VECCHIA_ERR_ARG;
+    if (!cov_ok(cov) || S < 2 || S > VECCHIA_MAX_S || N < 1 || N > INT_MAX) return VECCHIA_ERR_ARG;
+    if (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) return VECCHIA_ERR_ARG;
+    if (ni > VECCHIA_CENSOR_MAX_OBS || nc > INT_MAX / 2 || m > VECCHIA_MAX_M) return VECCHIA_ERR_UNSUPPORTED;
+    *log_g = NAN;
+    *std_err = NAN;
+    if (ni == 0)  // nothing observed: the CDF itself (Eq. model03, or Phi_D when R = 1)
+        return n_nodes == 0 ? vecchia_log_cdf(c, sites_c, nc, nbr, m, cov, x_c, N, S, seed, precision, log_g, std_err)
+                            : vecchia_mixture_log_cdf(c, sites_c, nc, nbr, m, cov, x_c, N, S, seed, beta, gamma,
+                                                      n_nodes, precision, log_g, std_err);
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    c->last_error_site = -1;
+    const bool dev = is_device_ptr(sites_i);
+    if (is_device_ptr(x_i) != dev || (nc > 0 && (is_device_ptr(sites_c) != dev || is_device_ptr(x_c) != dev)) ||
+        (nc > 0 && m > 0 && is_device_ptr(nbr) != dev))
+        return VECCHIA_ERR_ARG;
+    const int k = (int)ni;
+    Carve dv(nullptr);
+    const size_t o_si = dv.off;
+    if (!dev) dv.take<double>(2 * ni);
+    const size_t o_xi = dv.off;
+    if (!dev) dv.take<double>(ni);
+    const size_t o_sc = dv.off;
+    if (!dev) dv.take<double>(2 * nc);
+    const size_t o_xc = dv.off;
+    if (!dev) dv.take<double>(nc);
+    const size_t o_nb = dv.off;
+    if (!dev && m > 0) dv.take<int32_t>((size_t)nc * m);
+    const size_t o_L = dv.off;
+    dv.take<double>((size_t)k * k);
+    const size_t o_V = dv.off;
+    dv.take<double>((size_t)(nc + 1) * k);
+    const size_t o_u = dv.off;
+    dv.take<double>(nc);
+    const size_t o_bad = dv.off;
+    dv.take<int>(1);
+    int st = ensure_aux(c, dv.off);
+    if (st != VECCHIA_OK) return st;
+    char* X = (char*)c->aux;
+    const cudaStream_t s = c->stream;
+    const double* si = dev ? sites_i : (const double*)(X + o_si);
+    const double* xi = dev ? x_i : (const double*)(X + o_xi);
+    const double* sc = dev ? sites_c : (const double*)(X + o_sc);
+    const double* xc = dev ? x_c : (const double*)(X + o_xc);
+    const int32_t* nb = (dev || m == 0) ? nbr : (const int32_t*)(X + o_nb);
+    double* L = (double*)(X + o_L);
+    double* V = (double*)(X + o_V);
+    double* ud = (double*)(X + o_u);
+    int* bad = (int*)(X + o_bad);
+    cudaError_t e = cudaSuccess;
+    if (!dev) {
+        e = cudaMemcpyAsync(X + o_si, sites_i, sizeof(double) * 2 * ni, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(X + o_xi, x_i, sizeof(double) * ni, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && nc > 0)
+            e = cudaMemcpyAsync(X + o_sc, sites_c, sizeof(double) * 2 * nc, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && nc > 0) e = cudaMemcpyAsync(X + o_xc, x_c, sizeof(double) * nc, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && nc > 0 && m > 0)
+            e = cudaMemcpyAsync(X + o_nb, nbr, sizeof(int32_t) * nc * m, cudaMemcpyHostToDevice, s);
+    }
+    const int badinit = INT_MAX;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bad, &badinit, sizeof(int), cudaMemcpyHostToDevice, s);
+    // Sigma_II = L L^T; V = L^-1 Sigma_Ic, w = L^-1 x_I, thresholds x_c - V w
+    if (e == cudaSuccess) e = vk::launch_cov_chol(si, ni, cov, L, bad, s);
+    if (e == cudaSuccess) e = vk::launch_conditioning(L, k, si, xi, sc, xc, nc, cov, V, ud, s);
+    std::vector<double> diag((size_t)k), w((size_t)k);
+    int hbad = INT_MAX;
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(diag.data(), sizeof(double), L, sizeof(double) * (k + 1), sizeof(double), k,
+                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w.data(), V + (size_t)nc * k, sizeof(double) * k, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    if (hbad != INT_MAX) {
+        c->last_error_site = hbad;  // index among the observed sites
+        return VECCHIA_ERR_NOT_PD;
+    }
+    // log phi_k(x_I / r; Sigma_II) - k log r = -k/2 log 2 pi - log det L - |w|^2 / (2 r^2) - k log r
+    double logdetL = 0.0, quad = 0.0;
+    for (int t = 0; t < k; ++t) {
+        logdetL += std::log(diag[(size_t)t]);
+        quad += w[(size_t)t] * w[(size_t)t];
+    }
+    const double kLog2Pi = 1.8378770664093454836;
+    auto log_dens = [&](double r) { return -0.5 * k * kLog2Pi - logdetL - quad / (2.0 * r * r) - k * std::log(r); };
+    std::vector<double> rq, wq;
+    if (n_nodes == 0) {
+        rq.assign(1, 1.0);
+        wq.assign(1, 1.0);
+    } else {
+        mixture_nodes(n_nodes, beta, gamma, rq, wq);
+    }
+    const int nq = (int)rq.size();
+    std::vector<double> lp((size_t)nq, 0.0), se((size_t)nq, 0.0);
+    if (nc > 0) {
+        std::vector<vecchia_problem> probs((size_t)nq);
+        std::vector<double> scale((size_t)nq);
+        for (int q = 0; q < nq; ++q) {
+            vecchia_problem& p = probs[(size_t)q];
+            const double r2 = rq[(size_t)q] * rq[(size_t)q];
+            p.sites = sc;
+            p.nbr = nb;
+            p.u = ud;
+            p.D = nc;
+            p.m = m;
+            p.S = S;
+            p.N = N;
+            p.seed = seed;
+            p.cov = cov;  // Phi_c(y / r; Sigma_{c|I}) = Phi_c(y; r^2 Sigma_{c|I})
+            p.cov.variance = cov.variance * r2;
+            p.cov.nugget = cov.nugget * r2;
+            scale[(size_t)q] = r2;
+        }
+        std::vector<int32_t> stv((size_t)nq);
+        int rc = run_problems(c, probs.data(), nq, precision, lp.data(), se.data(), stv.data(), nullptr, nullptr,
+                              nullptr, V, k, scale.data());
+        if (rc != VECCHIA_OK) return rc;
+        for (int q = 0; q < nq; ++q)
+            if (stv[(size_t)q] != VECCHIA_OK) return stv[(size_t)q];
+    }
+    // log G_I = log sum_q w_q exp(lp_q + log density(r_q)), largest term factored out
+    std::vector<double> tq((size_t)nq);
+    double mx = -INFINITY;
+    for (int q = 0; q < nq; ++q) {
+        tq[(size_t)q] = std::log(wq[(size_t)q]) + lp[(size_t)q] + log_dens(rq[(size_t)q]);
+        mx = std::max(mx, tq[(size_t)q]);
+    }
+    double sum = 0.0;
+    for (int q = 0; q < nq; ++q) sum += std::exp(tq[(size_t)q] - mx);
+    *log_g = mx + std::log(sum);
+    double seb = 0.0;  // the nodes share shifts: bound by full correlation
+    for (int q = 0; q < nq; ++q) seb += std::exp(tq[(size_t)q] - *log_g) * se[(size_t)q];
+    *std_err = seb;
+    if (!std::isfinite(*log_g)) return VECCHIA_ERR_NONFINITE;
     return VECCHIA_OK;
 }
 

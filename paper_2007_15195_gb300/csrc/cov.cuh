@@ -3,6 +3,8 @@
 // the fields cov_kind, variance, range, nu, cos_a, sin_a, aspect.
 #pragma once
 
+#include <cmath>
+
 #include "vecchia.h"
 
 namespace vk {
@@ -29,6 +31,25 @@ __device__ __forceinline__ double cov_fn(int kind, double var, double range, dou
     }
     const double a = 2.2360679774997896964 * h / range;
     return var * (1.0 + a + a * a / 3.0) * exp(-a);
+}
+
+// Covariance parameters as the kernels read them (rotation precomputed).
+struct CovParams {
+    int cov_kind;
+    double variance, range, nu, nugget, cos_a, sin_a, aspect;
+};
+
+inline CovParams cov_params(const vecchia_cov& c) {
+    CovParams p;
+    p.cov_kind = c.kind;
+    p.variance = c.variance;
+    p.range = c.range;
+    p.nu = c.nu;
+    p.nugget = c.nugget;
+    p.cos_a = c.kind == VECCHIA_COV_ANISO_EXP ? std::cos(c.angle) : 1.0;
+    p.sin_a = c.kind == VECCHIA_COV_ANISO_EXP ? std::sin(c.angle) : 0.0;
+    p.aspect = c.kind == VECCHIA_COV_ANISO_EXP ? c.aspect : 1.0;
+    return p;
 }
 
 }  // namespace vk

@@ -34,12 +34,7 @@ constexpr int kCholB = 32;   // Cholesky block
 constexpr int kFullP = 128;  // lattice points per CTA (one per thread in the sequential part)
 constexpr int kFullKC = 32;  // history chunk of the contraction
 
-struct FullCov {
-    int cov_kind;
-    double variance, range, nu, nugget, cos_a, sin_a, aspect;
-};
-
-__global__ void full_cov_kernel(const double* __restrict__ sites, int D, FullCov cv, double* __restrict__ A) {
+__global__ void full_cov_kernel(const double* __restrict__ sites, int D, CovParams cv, double* __restrict__ A) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
     if (r >= D || c > r) return;
     const double h = site_dist(cv, __dsub_rn(sites[2 * r], sites[2 * c]), __dsub_rn(sites[2 * r + 1], sites[2 * c + 1]));
@@ -338,6 +333,24 @@ cudaError_t launch_full_genz_t(const double* A, const double* u, const FullArgs&
 
 }  // namespace
 
+cudaError_t launch_cov_chol(const double* sites, int64_t D, const vecchia_cov& cov, double* A, int* bad,
+                            cudaStream_t st) {
+    if (D <= 0) return cudaSuccess;
+    full_cov_kernel<<<dim3((unsigned)((D + 127) / 128), (unsigned)D), 128, 0, st>>>(sites, (int)D, cov_params(cov), A);
+    cudaError_t e = cudaGetLastError();
+    for (int64_t k0 = 0; k0 < D && e == cudaSuccess; k0 += kCholB) {
+        chol_diag_kernel<<<1, 32, 0, st>>>(A, (int)D, (int)k0, bad);
+        const int64_t rows = D - k0 - kCholB;
+        if (rows > 0) {
+            chol_trsm_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(A, (int)D, (int)k0);
+            const int64_t tiles = (rows + kCholB - 1) / kCholB;
+            chol_update_kernel<<<(unsigned)(tiles * (tiles + 1) / 2), 256, 0, st>>>(A, (int)D, (int)k0);
+        }
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 size_t full_genz_scratch_bytes(int64_t D, int64_t N, int S, bool mixed) {
     const size_t el = mixed ? 4 : 8;
     const int64_t bps = (N + kFullP - 1) / kFullP;
@@ -391,27 +404,7 @@ cudaError_t launch_full_genz(const double* sites, const double* u, int64_t D, co
     if (e != cudaSuccess) return e;
     e = launch_shifts(seed_d, S_d, off_d, 1, (int)dim, delta, dfix, st);
     if (e != cudaSuccess) return e;
-    FullCov cv;
-    cv.cov_kind = cov.kind;
-    cv.variance = cov.variance;
-    cv.range = cov.range;
-    cv.nu = cov.nu;
-    cv.nugget = cov.nugget;
-    cv.cos_a = cov.kind == VECCHIA_COV_ANISO_EXP ? cos(cov.angle) : 1.0;
-    cv.sin_a = cov.kind == VECCHIA_COV_ANISO_EXP ? sin(cov.angle) : 0.0;
-    cv.aspect = cov.kind == VECCHIA_COV_ANISO_EXP ? cov.aspect : 1.0;
-    full_cov_kernel<<<dim3((unsigned)((D + 127) / 128), (unsigned)D), 128, 0, st>>>(sites, (int)D, cv, A);
-    e = cudaGetLastError();
-    for (int64_t k0 = 0; k0 < D && e == cudaSuccess; k0 += kCholB) {
-        chol_diag_kernel<<<1, 32, 0, st>>>(A, (int)D, (int)k0, bad);
-        const int64_t rows = D - k0 - kCholB;
-        if (rows > 0) {
-            chol_trsm_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(A, (int)D, (int)k0);
-            const int64_t tiles = (rows + kCholB - 1) / kCholB;
-            chol_update_kernel<<<(unsigned)(tiles * (tiles + 1) / 2), 256, 0, st>>>(A, (int)D, (int)k0);
-        }
-        e = cudaGetLastError();
-    }
+    e = launch_cov_chol(sites, D, cov, A, bad, st);
     if (e != cudaSuccess) return e;
     FullArgs fa;
     fa.D = (int)D;

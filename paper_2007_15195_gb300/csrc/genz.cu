@@ -582,6 +582,13 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
                     const double h = site_dist(Pd, __dsub_rn(sm.bx[r], sm.bx[col]), __dsub_rn(sm.by[r], sm.by[col]));
                     double v = cov_fn(Pd.cov_kind, Pd.variance, Pd.range, Pd.nu, h);
                     if (col == r) v += Pd.nugget;
+                    if (Pd.lr_k > 0) {  // conditional covariance: minus scale V_a . V_b
+                        const double* Va = Pd.lr_V + (int64_t)sm.bidx[r] * Pd.lr_k;
+                        const double* Vb = Pd.lr_V + (int64_t)sm.bidx[col] * Pd.lr_k;
+                        double acc = 0.0;
+                        for (int t = 0; t < Pd.lr_k; ++t) acc = fma(Va[t], Vb[t], acc);
+                        v = v - Pd.lr_scale * acc;
+                    }
                     sm.A[r][col] = v;
                 }
             __syncwarp();

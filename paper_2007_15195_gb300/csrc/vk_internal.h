@@ -53,9 +53,12 @@ struct ProbDev {
     int64_t N;
     double variance, range, nu, nugget;
     double cos_a, sin_a, aspect;  // anisotropic exponential: rotation and aspect ratio
+    const double* lr_V;    // low-rank correction of the covariance (or nullptr): D x lr_k,
+    double lr_scale;       //   entry (a, b) -= lr_scale * V_a . V_b  (conditional covariance)
     int32_t cov_kind;
     int32_t m;
     int32_t group;         // 0: classic (term i = site i, N_i = min(m, i) nearest); p: groups of p
+    int32_t lr_k;          // columns of lr_V (0: no correction)
     int32_t S;
     int32_t dim;           // row stride of delta / dfix
     ProbResult* res;       // result slot owned by the caller (segment calls), or nullptr
@@ -128,6 +131,18 @@ cudaError_t launch_group_union(const int32_t* per_site, int64_t D, int m, int p,
 // group k (Floyd's algorithm on Philox4x32-10 draws), ascending.
 cudaError_t launch_group_random(int64_t D, int p, int kk, uint64_t seed, int cmax, int32_t* cond,
                                 int32_t* count, cudaStream_t st);
+
+// Covariance of D device sites (FP64, lower triangle of the D x D array A) and
+// its blocked Cholesky factor in place; *bad = min failing row (start INT_MAX).
+cudaError_t launch_cov_chol(const double* sites, int64_t D, const vecchia_cov& cov, double* A, int* bad,
+                            cudaStream_t st);
+// Conditioning on observed sites (censor.cu): with L the Cholesky factor of
+// Sigma_II (k x k, from launch_cov_chol on sites_i), rows a < nc of V
+// ((nc + 1) x k) get L^-1 Sigma_{I a}, row nc gets w = L^-1 x_I, and
+// u_out[a] = x_c[a] - V_a . w (the censored thresholds minus the conditional mean).
+cudaError_t launch_conditioning(const double* L, int k, const double* sites_i, const double* x_i,
+                                const double* sites_c, const double* x_c, int64_t nc, const vecchia_cov& cov,
+                                double* V, double* u_out, cudaStream_t st);
 
 // Full D-dimensional Genz estimate (full.cu): covariance, blocked FP64
 // Cholesky, Genz over all variables; part_host gets S x ceil(N/128) tile sums

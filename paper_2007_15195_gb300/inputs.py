@@ -82,6 +82,39 @@ def grid100(seed: int = 0, workload_seed: int = 0, N: int = 2048, S: int = 8) ->
                    name="grid100_exp0.1")
 
 
+@dataclass
+class CensoredReplicate:
+    """One replicate of a censored likelihood: values at the sites, the ones
+    above the threshold observed (x_obs at sites_obs), the others censored at
+    the threshold (x_cen = threshold at sites_cen)."""
+    sites_cen: np.ndarray
+    x_cen: np.ndarray
+    sites_obs: np.ndarray
+    x_obs: np.ndarray
+
+
+def censored_replicates(n_rep: int = 32, D: int = 528, frac_obs: float = 0.1, workload_seed: int = 0):
+    """The application's shape (Sec. 4.1): D = 528 station sites uniform in the
+    unit square (a stand-in for the stations, which are not available), the
+    anisotropic exponential covariance of Sec. 4.1 (range 0.2, angle 0.5,
+    aspect 1.5, unit variance), and per replicate a random frac_obs of the
+    sites above the threshold Phi^{-1}(0.9): their values are the threshold
+    plus Exp(1)/2, the others are censored at the threshold.  Returns the
+    covariance tuple and the replicates (sites not ordered)."""
+    s = rng(workload_seed, _STREAM_SITES).random((D, 2))
+    g = rng(workload_seed, _STREAM_M)
+    e = rng(workload_seed, _STREAM_U)
+    cov = (2, 1.0, 0.2, 0.5, 0.0, 0.5, 1.5)  # VECCHIA_COV_ANISO_EXP
+    reps = []
+    for _ in range(n_rep):
+        k = max(1, int(round(frac_obs * D)))
+        obs = np.sort(g.choice(D, size=k, replace=False))
+        cen = np.setdiff1d(np.arange(D), obs)
+        reps.append(CensoredReplicate(s[cen].copy(), np.full(cen.size, Z_090), s[obs].copy(),
+                                      Z_090 + 0.5 * e.exponential(size=k)))
+    return cov, reps
+
+
 def batch_problems(n_problems: int = 4096, workload_seed: int = 0, m: int = 20, N: int = 2048,
                    S: int = 8, d_lo: float = 50.0, d_hi: float = 2000.0) -> List[Problem]:
     """Independent problems: D log-uniform in [d_lo, d_hi], sites uniform in the
