@@ -561,11 +561,11 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
         const int groups = src.items ? 1 : src.groups;
         const int s_lo = (S * grp) / groups, s_hi = (S * (grp + 1)) / groups;
 
-        // ---- prologue: block, covariance, Cholesky (warp 0, FP64) ----
+        // ---- prologue: block (warp 0), covariance (all warps), Cholesky (warp 0); FP64 ----
         if (warp == 0) {
             int c = 0, d = 1;
             int64_t i0 = 0;
-            int bad = term_block<DMAX, MIXED>(sm, Pd, term, c, d, i0) ? 0 : 2;
+            const int bad = term_block<DMAX, MIXED>(sm, Pd, term, c, d, i0) ? 0 : 2;
             if (!bad)
                 for (int v = lane; v < d; v += 32) {
                     const int idx = sm.bidx[v];
@@ -573,31 +573,44 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
                     sm.by[v] = Pd.sites[2 * (int64_t)idx + 1];
                     sm.bu[v] = Pd.u[idx];
                 }
-            __syncwarp();
-            // covariance, lower triangle, entries packed over the lanes
-            if (!bad)
-                for (int e = lane; e < d * (d + 1) / 2; e += 32) {
-                    int r, col;
-                    tri_index(e, r, col);
-                    const double h = site_dist(Pd, __dsub_rn(sm.bx[r], sm.bx[col]), __dsub_rn(sm.by[r], sm.by[col]));
-                    double v = cov_fn(Pd.cov_kind, Pd.variance, Pd.range, Pd.nu, h);
-                    if (col == r) v += Pd.nugget;
-                    if (Pd.lr_k > 0) {  // conditional covariance: minus scale V_a . V_b
-                        const double* Va = Pd.lr_V + (int64_t)sm.bidx[r] * Pd.lr_k;
-                        const double* Vb = Pd.lr_V + (int64_t)sm.bidx[col] * Pd.lr_k;
-                        double acc = 0.0;
-                        for (int t = 0; t < Pd.lr_k; ++t) acc = fma(Va[t], Vb[t], acc);
-                        v = v - Pd.lr_scale * acc;
-                    }
-                    sm.A[r][col] = v;
+            if (lane == 0) {
+                sm.bad = bad;
+                sm.q = d - 1;
+                sm.c = c;
+                sm.flag = 0;
+            }
+        }
+        __syncthreads();
+        // covariance, lower triangle, entries packed over every thread (the
+        // FP64 units of all the CTA's warps)
+        if (!sm.bad) {
+            const int d = sm.q + 1;
+            for (int e = threadIdx.x; e < d * (d + 1) / 2; e += blockDim.x) {
+                int r, col;
+                tri_index(e, r, col);
+                const double h = site_dist(Pd, __dsub_rn(sm.bx[r], sm.bx[col]), __dsub_rn(sm.by[r], sm.by[col]));
+                double v = cov_fn(Pd.cov_kind, Pd.variance, Pd.range, Pd.nu, h);
+                if (col == r) v += Pd.nugget;
+                if (Pd.lr_k > 0) {  // conditional covariance: minus scale V_a . V_b
+                    const double* Va = Pd.lr_V + (int64_t)sm.bidx[r] * Pd.lr_k;
+                    const double* Vb = Pd.lr_V + (int64_t)sm.bidx[col] * Pd.lr_k;
+                    double acc = 0.0;
+                    for (int t = 0; t < Pd.lr_k; ++t) acc = fma(Va[t], Vb[t], acc);
+                    v = v - Pd.lr_scale * acc;
                 }
-            __syncwarp();
+                sm.A[r][col] = v;
+            }
+        }
+        __syncthreads();
+        if (warp == 0 && !sm.bad) {
+            const int d = sm.q + 1;
+            int bad = 0;
             // Cholesky, right-looking: after column j is final, the trailing
             // triangle takes its update fma(-L_rj, L_cj, A_rc), entries packed
             // over the lanes.  Each entry thus receives its terms in ascending
             // k with fma and is divided by the pivot last: the operations of
             // the row-by-row definition, in its order.
-            for (int j = 0; j < d && !bad; ++j) {
+            for (int j = 0; j < d; ++j) {
                 const double s = sm.A[j][j];
                 if (!(s > 0.0)) {  // warp-uniform: every lane reads the same value
                     bad = 1;
@@ -618,9 +631,6 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
             }
             if (lane == 0) {
                 sm.bad = bad;
-                sm.q = d - 1;
-                sm.c = c;
-                sm.flag = 0;
                 if (!bad) {
                     const double z0 = sm.bu[0] / sm.A[0][0];
                     phi_pair64(z0, sm.e0, sm.ec0);
