@@ -97,6 +97,16 @@ def dist_info():
     return world, rank, local
 
 
+def alu_roofline(work_ops, seconds, kernel, note=None):
+    """The roofline object for FP32-lane work done in `seconds`."""
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    r = {"bound": "alu", "achieved": work_ops / seconds / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+         "frac": work_ops / seconds / peak, "traffic": None, "kernel": kernel}
+    if note:
+        r["note"] = note
+    return r
+
+
 def alg_ops(D, m, N, S):
     q = np.minimum(np.arange(D), m).astype(np.float64)
     return float(N) * S * float(np.sum(q * ALG_OPS_STEP + q * (q + 1) / 2.0))
@@ -333,6 +343,10 @@ def run_ours(args):
         for prec, name in ((V.MIXED, "mixed"), (V.FP64, "fp64")):
             lp_f, se_f = V.vecchia_full_genz(ctx, s_f, prob.cov, u_f, N, S, seed=0, precision=prec)
             full[name] = {"log_p": lp_f, "rel_se": se_f, "ms": V.vecchia_genz_time_ms(ctx)}
+        # per point: the contraction and in-panel terms (D (D - 1) / 2 FMAs) and 34 ops per variable
+        work_f = float(N) * S * (D * (D - 1) / 2.0 + ALG_OPS_STEP * D)
+        full["mixed"]["roofline"] = alu_roofline(work_f, full["mixed"]["ms"] / 1000.0,
+                                                 "full Genz (covariance, FP64 Cholesky, panels)")
         lp_v = res_mixed[0][0]
         full["vecchia_mixed_log_p"] = lp_v
         full["vecchia_minus_full"] = lp_v - full["fp64"]["log_p"]
@@ -444,6 +458,7 @@ def run_serving(args):
         reqs = requests_from_stream(inputs.serving_stream(n_requests=args.serve_requests, rate_hz=rate))
         stats = srv.run(reqs)
         steps = sum(float(np.sum(np.minimum(np.arange(r.D), r.m))) for r in reqs) * 2048 * 8
+        work = sum(alg_ops(r.D, r.m, 2048, 8) for r in reqs)
         line = {"metric": "Vecchia log-CDF serving: requests/s and p50/p99 latency",
                 "value": stats["throughput_rps"], "unit": "requests/s", "n_gpus": 1,
                 "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
@@ -452,7 +467,9 @@ def run_serving(args):
                                        "N=2048 x S=8, xy order" % (rate, len(reqs)),
                            "precision": "mixed", "hbm_budget_bytes": srv.budget, "max_active": srv.max_active,
                            "chunk_sites": srv.chunk, "iter_sites": srv.iter_sites},
-                "offered_rps": rate, "genz_steps_per_s": steps / max(stats["wall_s"], 1e-9)}
+                "offered_rps": rate, "genz_steps_per_s": steps / max(stats["wall_s"], 1e-9),
+                "roofline": alu_roofline(work, max(stats["wall_s"], 1e-9), "genz_kernel (mixed), whole serving run",
+                                         "wall-clock of the run (arrival gaps included)")}
         line.update({k: stats[k] for k in ("completed", "submitted", "ok", "p50_ms", "p99_ms", "wait_p50_ms",
                                            "wait_p99_ms", "iterations", "wall_s", "peak_resident_bytes")})
         print(json.dumps(line))
@@ -647,7 +664,9 @@ def run_grouped(args):
             "config": {"workload": "grouped: 100x100 grid, exponential range 0.1, u~N(0.5,0.25^2), "
                                    "N=2048 x S=8, xy order, p in {2,5,10}, m=5", "precision": "mixed",
                        "step": "vecchia_grouped_log_cdf on resident device arrays"},
-            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "configs": rows}
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "configs": rows,
+            "roofline": dict(alu_roofline(head["alu_frac"] * SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6, 1.0,
+                                          "genz_kernel (mixed), p=5 nearest"))}
     print(json.dumps(line))
     ctx.close()
 
@@ -667,6 +686,7 @@ def run_censored(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     ctx = V.Context(0)
+    V.vecchia_set_timing(ctx, True)
     cov, reps = inputs.censored_replicates()
     m, N, S, n_nodes = 20, 2048, 8, 16
     data = []
@@ -677,11 +697,14 @@ def run_censored(args):
         dsc = t(sc)
         data.append((dsc, V.vecchia_neighbors(ctx, dsc, m), t(r.sites_obs), t(xc), t(r.x_obs)))
 
+    genz_ms = []
+
     def step(seed):
         tot = 0.0
         for dsc, nbr, dsi, dxc, dxi in data:
             lg, _ = V.vecchia_censored_log_cdf(ctx, dsc, nbr, m, dsi, cov, dxc, dxi, N, S, seed=seed, beta=0.5,
                                                gamma=1.0, n_nodes=n_nodes, precision=V.MIXED)
+            genz_ms.append(V.vecchia_genz_time_ms(ctx))
             tot += lg
         return tot
 
@@ -694,6 +717,8 @@ def run_censored(args):
         ll = step(k)
         ms.append(1000.0 * (time.perf_counter() - t0))
     ms = np.array(ms)
+    work = n_nodes * sum(alg_ops(int(d[0].shape[0]), m, N, S) for d in data)
+    genz_s = float(np.sum(genz_ms[-len(data) * args.steps:])) / 1000.0 / args.steps
     line = {"metric": "censored log-likelihood evals/s (528 sites, 32 replicates, 16 nodes)",
             "value": 1000.0 / float(ms.mean()), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
@@ -703,7 +728,9 @@ def run_censored(args):
                                    "N=2048 x S=8, beta=0.5 gamma=1, 16 nodes", "precision": "mixed",
                        "step": "sum over replicates of vecchia_censored_log_cdf (resident device arrays)"},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-            "log_likelihood": ll, "per_replicate_ms": float(ms.mean()) / len(data)}
+            "log_likelihood": ll, "per_replicate_ms": float(ms.mean()) / len(data),
+            "roofline": dict(alu_roofline(work, genz_s, "genz_kernel (mixed) with the conditional covariance"),
+                             kernel_ms=genz_s * 1000.0)}
     print(json.dumps(line))
     ctx.close()
 
