@@ -140,6 +140,17 @@ int vecchia_log_cdf_terms(vecchia_ctx* ctx, const double* sites_ordered, int64_t
                           int S, uint64_t seed, int precision, double* log_p, double* std_err,
                           double* terms, double* num, double* den);
 
+/* Steps a0-a7 in one call from unordered sites: the ordering (order_kind),
+ * its application, the m-neighbour rows and the log-CDF, queued on the
+ * context's stream with no host round trip in between (the XY ordering of
+ * more than 8192 sites is the one host step); the same results as the four
+ * calls in sequence.  sites (D x 2) and u (D) host or device, both of one
+ * kind; perm_out (D, host or device) may be NULL, else it gets the ordering
+ * (new position -> old index).  Other arguments as for vecchia_log_cdf. */
+int vecchia_log_cdf_unordered(vecchia_ctx* ctx, const double* sites, const double* u, int64_t D, int order_kind,
+                              int m, vecchia_cov cov, int64_t N, int S, uint64_t seed, int precision,
+                              int32_t* perm_out, double* log_p, double* std_err);
+
 /* One problem of a batch: the arguments of vecchia_log_cdf, or, with
  * group = p >= 1, of vecchia_grouped_log_cdf (nbr then holds the
  * ceil(D/p) x m conditioning rows of the groups and m is cmax). */

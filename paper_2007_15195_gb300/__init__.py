@@ -13,6 +13,7 @@ from .binding import (COND_NEAREST, COND_RANDOM, COV_ANISO_EXP, COV_EXPONENTIAL,
                       vecchia_genz_time_ms,
                       vecchia_group_conditioning, vecchia_grouped_log_cdf, vecchia_last_error_site,
                       vecchia_lattice, vecchia_log_cdf, vecchia_log_cdf_batch, vecchia_log_cdf_terms,
+                      vecchia_log_cdf_unordered,
                       vecchia_mixture_log_cdf, vecchia_neighbors, vecchia_order, vecchia_plan_create,
                       vecchia_reset_tiles, vecchia_set_tile, vecchia_set_timing, vecchia_shifts)
 
@@ -22,7 +23,7 @@ __all__ = [
     "make_cov", "vecchia_censored_log_cdf", "vecchia_create", "vecchia_destroy", "vecchia_apply_order", "vecchia_full_genz",
     "vecchia_genz_time_ms",
     "vecchia_group_conditioning", "vecchia_grouped_log_cdf", "vecchia_last_error_site", "vecchia_lattice",
-    "vecchia_log_cdf", "vecchia_log_cdf_batch", "vecchia_log_cdf_terms", "vecchia_mixture_log_cdf",
+    "vecchia_log_cdf", "vecchia_log_cdf_batch", "vecchia_log_cdf_terms", "vecchia_log_cdf_unordered", "vecchia_mixture_log_cdf",
     "vecchia_neighbors", "vecchia_order", "vecchia_reset_tiles", "vecchia_set_tile", "vecchia_set_timing",
     "vecchia_shifts",
 ]

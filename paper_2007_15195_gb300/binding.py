@@ -112,6 +112,9 @@ def lib():
         L.vecchia_censored_log_cdf.argtypes = [_vp, _vp, C.c_int64, _vp, C.c_int, _vp, C.c_int64, vecchia_cov, _vp,
                                                _vp, C.c_int64, C.c_int, C.c_uint64, C.c_double, C.c_double,
                                                C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.vecchia_log_cdf_unordered.argtypes = [_vp, _vp, _vp, C.c_int64, C.c_int, C.c_int, vecchia_cov, C.c_int64,
+                                                C.c_int, C.c_uint64, C.c_int, _vp, C.POINTER(C.c_double),
+                                                C.POINTER(C.c_double)]
         L.vecchia_lattice.argtypes = [C.c_int64, C.c_int, _vp]
         L.vecchia_shifts.argtypes = [C.c_uint64, C.c_int, C.c_int, _vp]
         L.vecchia_last_error_site.restype = C.c_int64
@@ -335,6 +338,19 @@ def vecchia_censored_log_cdf(ctx, sites_c, nbr, m, sites_i, cov, x_c, x_i, N, S,
                                           float(beta), float(gamma), int(n_nodes), int(precision), C.byref(lg),
                                           C.byref(se)), "vecchia_censored_log_cdf", ctx)
     return lg.value, se.value
+
+
+def vecchia_log_cdf_unordered(ctx, sites, u, m, cov, N, S, seed=0, precision=MIXED, order="xy", perm_out=None):
+    """Order, neighbours and the log-CDF in one call from unordered sites;
+    returns (log_p, std_err).  perm_out: optional int32 array of D (host or
+    device) that receives the ordering."""
+    s, uu = _f64(sites), _f64(u)
+    k = ORDER_KINDS.get(order, order) if isinstance(order, str) else int(order)
+    lp, se = C.c_double(), C.c_double()
+    _check(lib().vecchia_log_cdf_unordered(ctx.handle, _ptr(s), _ptr(uu), s.shape[0], k, int(m), make_cov(cov),
+                                           int(N), int(S), C.c_uint64(int(seed)), int(precision), _ptr(perm_out),
+                                           C.byref(lp), C.byref(se)), "vecchia_log_cdf_unordered", ctx)
+    return lp.value, se.value
 
 
 def vecchia_mixture_log_cdf(ctx, sites_ordered, nbr, m, cov, x, N, S, seed=0, beta=0.5, gamma=1.0,

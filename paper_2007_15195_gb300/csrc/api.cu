@@ -1078,6 +1078,100 @@ int vecchia_apply_order(vecchia_ctx* c, const int32_t* perm, const double* sites
     return VECCHIA_OK;
 }
 
+int vecchia_log_cdf_unordered(vecchia_ctx* c, const double* sites, const double* u, int64_t D, int order_kind,
+                              int m, vecchia_cov cov, int64_t N, int S, uint64_t seed, int precision,
+                              int32_t* perm_out, double* log_p, double* std_err) {
+    if (!c || !sites || !u || !log_p || !std_err || D < 1 || D > INT_MAX / 2 || m < 0) return VECCHIA_ERR_ARG;
+    if (order_kind != VECCHIA_ORDER_XY && order_kind != VECCHIA_ORDER_MAXMIN && order_kind != VECCHIA_ORDER_IDENTITY)
+        return VECCHIA_ERR_ARG;
+    if (m > VECCHIA_MAX_M) return VECCHIA_ERR_UNSUPPORTED;
+    *log_p = NAN;
+    *std_err = NAN;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    const bool dev = is_device_ptr(sites);
+    if (is_device_ptr(u) != dev) return VECCHIA_ERR_ARG;
+    const bool host_xy = order_kind == VECCHIA_ORDER_XY && D > vk::kOrderXyDeviceMax;
+    Carve dv(nullptr);
+    const size_t o_s = dv.off;
+    if (!dev) dv.take<double>(2 * D);
+    const size_t o_u = dv.off;
+    if (!dev) dv.take<double>(D);
+    const size_t o_perm = dv.off;
+    dv.take<int32_t>(D);
+    const size_t o_so = dv.off;
+    dv.take<double>(2 * D);
+    const size_t o_uo = dv.off;
+    dv.take<double>(D);
+    const size_t o_nbr = dv.off;
+    dv.take<int32_t>((size_t)D * std::max(m, 1));
+    const size_t o_bad = dv.off;
+    dv.take<int>(1);
+    const size_t o_scr = dv.off;
+    dv.take<char>(std::max(std::max(vk::knn_scratch_bytes(D), vk::order_xy_scratch_bytes(D)),
+                           order_kind == VECCHIA_ORDER_MAXMIN ? vk::maxmin_scratch_bytes(D) : (size_t)0));
+    int st = ensure_aux(c, dv.off);
+    if (st != VECCHIA_OK) return st;
+    char* X = (char*)c->aux;
+    const cudaStream_t s = c->stream;
+    const double* sd = dev ? sites : (const double*)(X + o_s);
+    const double* ud = dev ? u : (const double*)(X + o_u);
+    int32_t* perm = (int32_t*)(X + o_perm);
+    double* so = (double*)(X + o_so);
+    double* uo = (double*)(X + o_uo);
+    int32_t* nbr = (int32_t*)(X + o_nbr);
+    cudaError_t e = cudaSuccess;
+    if (!dev) {
+        e = cudaMemcpyAsync(X + o_s, sites, sizeof(double) * 2 * D, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(X + o_u, u, sizeof(double) * D, cudaMemcpyHostToDevice, s);
+    }
+    // ordering, queued on the stream (the host sort only for XY beyond the device size)
+    std::vector<int32_t> hp;
+    if (e == cudaSuccess) {
+        if (order_kind == VECCHIA_ORDER_MAXMIN) {
+            e = vk::launch_maxmin(sd, D, perm, X + o_scr, s);
+        } else if (order_kind == VECCHIA_ORDER_XY && !host_xy) {
+            e = vk::launch_order_xy(sd, D, perm, X + o_scr, s);
+        } else {
+            hp.resize((size_t)D);
+            if (order_kind == VECCHIA_ORDER_XY) {
+                st = vecchia_order(dev ? c : nullptr, sites, D, VECCHIA_ORDER_XY, hp.data());
+                if (st != VECCHIA_OK) return st;
+            } else {
+                for (int64_t k = 0; k < D; ++k) hp[(size_t)k] = (int32_t)k;
+            }
+            e = cudaMemcpyAsync(perm, hp.data(), sizeof(int32_t) * D, cudaMemcpyHostToDevice, s);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(X + o_bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = vk::launch_gather(perm, sd, ud, D, so, uo, (int*)(X + o_bad), s);
+    if (e == cudaSuccess && m > 0) e = vk::launch_knn(so, D, m, nbr, X + o_scr, s);
+    if (e == cudaSuccess && !hp.empty()) e = cudaStreamSynchronize(s);  // hp must outlive its upload
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    vecchia_problem p{};
+    p.sites = so;
+    p.nbr = m > 0 ? nbr : nullptr;
+    p.u = uo;
+    p.D = D;
+    p.m = m;
+    p.S = S;
+    p.N = N;
+    p.seed = seed;
+    p.cov = cov;
+    int32_t status = VECCHIA_OK;
+    st = run_problems(c, &p, 1, precision, log_p, std_err, &status, nullptr, nullptr, nullptr);
+    if (perm_out && (st == VECCHIA_OK || st == VECCHIA_ERR_NOT_PD)) {
+        if (cudaMemcpyAsync(perm_out, perm, sizeof(int32_t) * D, cudaMemcpyDefault, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return VECCHIA_ERR_CUDA;
+        }
+    }
+    return st;
+}
+
 int vecchia_neighbors(vecchia_ctx* c, const double* sites, int64_t D, int m, int32_t* nbr) {
     if (!c || !sites || D < 1 || D > INT_MAX / 2 || m < 0) return VECCHIA_ERR_ARG;
     if (m > VECCHIA_MAX_M) return VECCHIA_ERR_UNSUPPORTED;

@@ -253,3 +253,25 @@ def test_device_xy_order_equals_oracle(ctx, D, kind):
     ref = O.order(s, O.ORDER_XY)
     got = B.vecchia_order(ctx, torch.from_numpy(s).cuda(), "xy")
     assert np.array_equal(got.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("order,D,m,device", [("xy", 2500, 20, True), ("xy", 2500, 20, False), ("maxmin", 1500, 12, True),
+                                              ("identity", 700, 8, False), ("xy", 9000, 5, True)])
+def test_unordered_call_equals_the_four_calls(ctx, order, D, m, device):
+    """vecchia_log_cdf_unordered gives exactly the results of order, apply_order,
+    neighbors and log_cdf called one after the other."""
+    import torch
+    prob = inputs.grid50(m=m) if D == 2500 else inputs.small_random(D, D, m=m, N=512, S=4)
+    s, u = prob.sites, prob.u
+    if device:
+        s, u = torch.from_numpy(s).cuda(), torch.from_numpy(u).cuda()
+    perm = B.vecchia_order(ctx if device else None, s, order)
+    so, uo = B.vecchia_apply_order(ctx if device else None, perm, s, u)
+    nbr = B.vecchia_neighbors(ctx, so, m)
+    ref = B.vecchia_log_cdf(ctx, so, nbr, m, prob.cov, uo, prob.N, prob.S, 3, B.MIXED)
+    got_perm = np.zeros(D, np.int32)
+    got = B.vecchia_log_cdf_unordered(ctx, s, u, m, prob.cov, prob.N, prob.S, 3, B.MIXED, order=order,
+                                      perm_out=got_perm)
+    assert got == ref
+    p_ref = perm.cpu().numpy() if device else perm
+    assert np.array_equal(got_perm, p_ref)
