@@ -195,6 +195,18 @@ def test_grid50_m20_full_both_paths(ctx, grid50_m20):
     assert abs(mlp - lp) <= mixed_tol(lp), (mlp, lp)
 
 
+def test_grid50_m20_benchmark_call(ctx, grid50_m20):
+    """The call and configuration bench.py times (raw sites on the device,
+    vecchia_log_cdf_unordered, XY order, mixed and FP64) against the oracle."""
+    prob, s, u, nbr, num, den, lp, se, terms = grid50_m20
+    import torch
+    rs, ru = torch.from_numpy(prob.sites).cuda(), torch.from_numpy(prob.u).cuda()
+    mlp, mse = B.vecchia_log_cdf_unordered(ctx, rs, ru, 20, prob.cov, prob.N, prob.S, prob.seed, B.MIXED)
+    assert abs(mlp - lp) <= mixed_tol(lp), (mlp, lp)
+    flp, fse = B.vecchia_log_cdf_unordered(ctx, rs, ru, 20, prob.cov, prob.N, prob.S, prob.seed, B.FP64)
+    assert abs(flp - lp) <= FP64_TOL * abs(lp) and fse == pytest.approx(se, rel=1e-8)
+
+
 @pytest.mark.parametrize("m", [5, 10, 30])
 def test_grid50_sampled_terms(ctx, m):
     prob = inputs.grid50(m=m)
