@@ -377,10 +377,11 @@ int vecchia_eval_special(vecchia_ctx* ctx, int which, const float* x, int64_t n,
 #define VECCHIA_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /* vecchia_log_cdf for callers that cannot allocate memory (the paper has no
- * counterpart; this is a deployment variant of the same kernels).  Code that
- * runs while a CUDA graph is being captured, programs whose allocator owns the
- * whole device and forbids foreign cudaMalloc calls, and hosts that keep no
- * vecchia_ctx cannot use the context's scratch arena.  This entry point keeps
+ * counterpart; this is a deployment variant of the same kernels).  Programs
+ * whose allocator owns the whole device and forbids foreign cudaMalloc calls,
+ * code that must run within a fixed memory budget (no allocation after
+ * start-up), and hosts that keep no vecchia_ctx cannot use the context's
+ * scratch arena.  This entry point keeps
  * all of its scratch in one file-scope device array of
  * VECCHIA_NOALLOC_SCRATCH_BYTES (32 MiB, held by every GPU that loads the
  * library until the process exits) and calls no allocating routine: no

@@ -1,9 +1,9 @@
 // noalloc.cu -- vecchia_log_cdf_noalloc: the log-CDF without any allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// log-CDF: code running while a CUDA graph is being captured, allocators
-// that own the whole device and forbid foreign cudaMalloc calls, or hosts
-// that have no context object of ours.  This entry point runs the same
+// log-CDF: programs whose allocator owns the whole device and forbids foreign
+// cudaMalloc calls, code that must run within a fixed memory budget (no
+// allocation after start-up), or hosts that have no context object of ours.  This entry point runs the same
 // kernels as vecchia_log_cdf but keeps every piece of scratch (per-shift
 // partial sums, shift tables, lattice table, parameters, results) in one
 // file-scope device array of fixed size, so it calls no cudaMalloc, no

@@ -1,7 +1,7 @@
 """The scratch-free entry point vecchia_log_cdf_noalloc against vecchia_log_cdf.
 
 It serves callers that cannot allocate device memory where they evaluate a
-log-CDF (inside CUDA graph capture, under an allocator that owns the device,
+log-CDF (under an allocator that owns the device, within a fixed memory budget,
 without a context object).  Its scratch lives in a fixed device array that
 every call reuses, so the test calls it twice in a row on different problems,
 and compares each result with the context-based entry point on the same
