@@ -113,6 +113,10 @@ CASES = [
     ("rand_m31", lambda: inputs.small_random(120, 6, m=31, N=256, S=3)),
     ("D_lt_m", lambda: inputs.small_random(9, 7, m=20, N=640, S=6)),
     ("D1", lambda: inputs.small_random(1, 8, m=5, N=64, S=2)),
+    ("S64_max_shifts", lambda: inputs.small_random(100, 9, m=10, N=128, S=64)),
+    ("N1_one_point", lambda: inputs.small_random(40, 10, m=5, N=1, S=2)),
+    ("N3_odd", lambda: inputs.small_random(60, 11, m=6, N=3, S=3)),
+    ("m63_max", lambda: inputs.small_random(80, 12, m=63, N=128, S=2)),
 ]
 
 
