@@ -67,6 +67,33 @@ ALG_OPS_STEP = 34
 # the Genz kernel on the headline workload (m = 20, built-in tile:
 # genz_kernel<21, 2, fast>), from one ncu capture of that launch.
 GENZ_TRAFFIC_BYTES_M20 = 364_032
+# DRAM bytes of one launch of the full-Genz recursion kernel on the tensor
+# cores (full_genz_tc_kernel, 50x50 grid, D = 2,500, N = 4,096 x S = 16), from
+# one ncu capture of that launch: 26.79 GB read + 1.66 GB written.
+FULL_TC_TRAFFIC_BYTES_D2500 = 28_442_826_000
+FULL_TC_POINTS, FULL_TC_PANEL, FULL_TC_CHUNK = 224, 64, 16
+
+
+def hbm_peak_gbs():
+    """The measured copy bandwidth of this GPU type (GB/s) and its source."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def full_tc_bytes(D, N, S):
+    """DRAM bytes the tensor-core full-Genz kernel moves by design: every panel
+    of 64 variables re-reads the y history of its tile (hi and lo, 224 rows of
+    each 16-variable chunk) below the panel, and each chunk is written once."""
+    Dp = -(-D // FULL_TC_PANEL) * FULL_TC_PANEL
+    n_p = Dp // FULL_TC_PANEL
+    tiles = S * -(-N // FULL_TC_POINTS)
+    chunk = 2 * FULL_TC_POINTS * FULL_TC_CHUNK * 4
+    reads = tiles * (FULL_TC_PANEL // FULL_TC_CHUNK) * n_p * (n_p - 1) // 2 * chunk
+    writes = tiles * (Dp // FULL_TC_CHUNK) * chunk
+    return reads + writes
 
 
 def parse():
@@ -333,13 +360,28 @@ def run_ours(args):
         perm_f = V.vecchia_order(ctx, sites_d, "xy")
         s_f, u_f = V.vecchia_apply_order(ctx, perm_f, sites_d, u_d)
         full = {}
+        V.vecchia_full_genz(ctx, s_f, prob.cov, u_f, N, S, seed=1, precision=V.MIXED)  # scratch, attributes
         for prec, name in ((V.MIXED, "mixed"), (V.FP64, "fp64")):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             lp_f, se_f = V.vecchia_full_genz(ctx, s_f, prob.cov, u_f, N, S, seed=0, precision=prec)
-            full[name] = {"log_p": lp_f, "rel_se": se_f, "ms": V.vecchia_genz_time_ms(ctx)}
-        # per point: the contraction and in-panel terms (D (D - 1) / 2 FMAs) and 34 ops per variable
-        work_f = float(N) * S * (D * (D - 1) / 2.0 + ALG_OPS_STEP * D)
-        full["mixed"]["roofline"] = alu_roofline(work_f, full["mixed"]["ms"] / 1000.0,
-                                                 "full Genz (covariance, FP64 Cholesky, panels)")
+            call_ms = 1000.0 * (time.perf_counter() - t0)
+            full[name] = {"log_p": lp_f, "rel_se": se_f, "kernel_ms": V.vecchia_genz_time_ms(ctx),
+                          "call_ms": call_ms}
+        # the recursion kernel of the mixed path streams the y history through
+        # the tensor cores: bound by HBM at its panel width
+        t_k = full["mixed"]["kernel_ms"] / 1000.0
+        hbm, src = hbm_peak_gbs()
+        nbytes = full_tc_bytes(D, N, S)
+        ach = nbytes / t_k / 1e9
+        full["mixed"]["roofline"] = {
+            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": FULL_TC_TRAFFIC_BYTES_D2500 if (D == 2500 and N * S == 65536) else None,
+            "kernel": "full_genz_tc_kernel", "peak_source": src,
+            "bytes": "y history re-read per panel of 64 variables (hi and lo) + written once: %d per launch" % nbytes,
+            "contraction_tflops": float(N) * S * D * (D - 1) / t_k / 1e12,
+            "contraction_note": "the conditional-mean products of all D(D-1)/2 pairs, counted as FP32 FMAs "
+                                "(2 flops); the tensor cores run each as three TF32 products"}
         lp_v = res_mixed[0][0]
         full["vecchia_mixed_log_p"] = lp_v
         full["vecchia_minus_full"] = lp_v - full["fp64"]["log_p"]

@@ -361,7 +361,8 @@ int vecchia_set_tile(vecchia_ctx* ctx, int precision, int bucket, int warps, int
                      int slices, int groups);
 /* Back to the built-in tile rule for every precision and bucket. */
 int vecchia_reset_tiles(vecchia_ctx* ctx);
-/* Record CUDA events around the Genz launches of each call (0 = off). */
+/* Record CUDA events around the Genz launches of each call (0 = off); for
+ * vecchia_full_genz, around its recursion kernel alone. */
 int vecchia_set_timing(vecchia_ctx* ctx, int enable);
 /* Milliseconds between those events in the last call with timing on. */
 int vecchia_genz_time_ms(const vecchia_ctx* ctx, double* ms);

@@ -1377,18 +1377,17 @@ int vecchia_full_genz(vecchia_ctx* c, const double* sites, int64_t D, vecchia_co
     char* A = (char*)c->arena;
     const double* sd = dev_in ? sites : (const double*)(A + o_s);
     const double* ud = dev_in ? u : (const double*)(A + o_u);
-    const int64_t bps = (N + 127) / 128;
+    const int64_t bps = vk::full_genz_blocks_per_shift(N, mixed);
     std::vector<double> part((size_t)(S * bps));
-    int bad = INT_MAX;
+    int bad = INT_MAX, timed_out = 0;
     cudaError_t e = cudaSuccess;
     if (!dev_in) e = cudaMemcpyAsync(A + o_s, sites, sizeof(double) * 2 * D, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && !dev_in)
         e = cudaMemcpyAsync(A + o_u, u, sizeof(double) * D, cudaMemcpyHostToDevice, c->stream);
-    if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev0, c->stream);
     if (e == cudaSuccess)
         e = vk::launch_full_genz(sd, ud, D, cov, N, S, mixed, g.data(), gfix.data(), seed, A + o_scr, part.data(),
-                                 &bad, c->stream);
-    if (c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+                                 &bad, &timed_out, c->timing ? c->ev0 : nullptr, c->timing ? c->ev1 : nullptr,
+                                 c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1403,6 +1402,7 @@ int vecchia_full_genz(vecchia_ctx* c, const double* sites, int64_t D, vecchia_co
         c->last_error_site = bad;
         return VECCHIA_ERR_NOT_PD;
     }
+    if (timed_out) return VECCHIA_ERR_TIMEOUT;
     // per-shift means (tile sums in order), their mean and relative standard error
     std::vector<double> ps((size_t)S);
     double mean = 0.0;

@@ -10,21 +10,22 @@
 //      rows below it, and the trailing update.  Every entry receives its
 //      terms in ascending k with fma and the pivot division last: the
 //      operations of the row-by-row definition in its order;
-//   3. the rows of L scaled by 1/L_vv (u likewise), in the path's precision;
-//   4. Genz's recursion for CTA tiles of P = 128 lattice points, in panels of
-//      B variables: the panel's conditional means u_v - sum_{t < v0} L_vt y_t
-//      are a register-tiled contraction of the panel's rows of L with the
-//      stored y history (smem-staged chunks of 32 variables), then one thread
-//      per point runs the panel's variables in order (the in-panel terms,
-//      Phi, the running product in FP64, Phi^{-1} of the lattice-weighted
-//      probability) and appends its y values to the history;
-//   5. per-tile sums of the point products, added per shift in a fixed order.
+//   3. the rows of L scaled by 1/L_vv (u likewise);
+//   4. Genz's recursion.  FP64 (here): CTA tiles of P = 128 lattice points, in
+//      panels of 32 variables: the panel's conditional means
+//      u_v - sum_{t < v0} L_vt y_t are a register-tiled contraction of the
+//      panel's rows of L with the stored y history (smem-staged chunks of 32
+//      variables), then one thread per point runs the panel's variables in
+//      order (the in-panel terms, Phi, the running product, Phi^{-1} of the
+//      lattice-weighted probability) and appends its y values to the history.
+//      Mixed: the same recursion with the contraction on the tensor cores
+//      (full_tc.cu);
+//   5. per-block sums of the point products, added per shift in a fixed order.
 #include <climits>
 #include <map>
 #include <mutex>
 
 #include "cov.cuh"
-#include "special_f32.h"
 #include "vk_internal.h"
 
 namespace vk {
@@ -157,12 +158,8 @@ __global__ void full_tables_kernel(const double* __restrict__ A, const double* _
 template <class T>
 struct FullTraits;
 template <>
-struct FullTraits<float> {
-    static constexpr int B = 64, TJ = 8, TP = 8;  // panel width; per-thread tile (variables x points)
-};
-template <>
 struct FullTraits<double> {
-    static constexpr int B = 32, TJ = 4, TP = 8;
+    static constexpr int B = 32, TJ = 4, TP = 8;  // panel width; per-thread tile (variables x points)
 };
 
 struct FullArgs {
@@ -170,15 +167,12 @@ struct FullArgs {
     int64_t N;
     int S;
     int blocks_per_shift;
-    const uint32_t* g;     // lattice vector (FP64 path), D - 1 entries
-    const uint32_t* gfix;  // round(g 2^32 / N) (FP32 path)
-    const double* delta;   // S x dim shifts (FP64 path)
-    const uint32_t* dfix;  // S x dim, top 32 bits (FP32 path)
-    int dim;               // row stride of delta / dfix
+    const uint32_t* g;     // lattice vector, D - 1 entries
+    const double* delta;   // S x dim shifts
+    int dim;               // row stride of delta
 };
 
-// e = Phi(z), ec = 1 - e, in the path's precision.
-__device__ __forceinline__ void full_phi(float z, float& e, float& ec) { special::phi_pair_fast(z, e, ec); }
+// e = Phi(z), ec = 1 - e.
 __device__ __forceinline__ void full_phi(double z, double& e, double& ec) {
     const double t = normcdf(-fabs(z));
     e = (z < 0.0) ? t : 1.0 - t;
@@ -186,13 +180,6 @@ __device__ __forceinline__ void full_phi(double z, double& e, double& ec) {
 }
 
 // y = Phi^{-1}(w e) at lattice coordinate v of point k of shift s.
-__device__ __forceinline__ float full_y(const FullArgs& a, int s, uint32_t k, int v, float e, float ec) {
-    const uint32_t X = k * a.gfix[v] + a.dfix[(int64_t)s * a.dim + v];
-    const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
-    const float w = __fmul_rn(__uint2float_rn(V), 0x1p-31f);
-    const float am = __fmul_rn(__uint2float_rn(0x80000000u - V), 0x1p-31f);  // |2x - 1|
-    return special::phiinv_pq(__fmul_rn(w, e), fmaf(w, ec, am));
-}
 __device__ __forceinline__ double full_y(const FullArgs& a, int s, uint32_t k, int v, double e, double ec) {
     const uint64_t rr = ((uint64_t)k * (uint64_t)a.g[v]) % (uint64_t)a.N;
     double x = __dadd_rn((double)rr / (double)a.N, a.delta[(int64_t)s * a.dim + v]);
@@ -308,7 +295,7 @@ size_t full_smem_bytes() {
 
 template <class T>
 cudaError_t launch_full_genz_t(const double* A, const double* u, const FullArgs& a, void* Ls, void* us, void* Y,
-                               double* part, cudaStream_t st) {
+                               double* part, cudaEvent_t ev_begin, cudaEvent_t ev_end, cudaStream_t st) {
     const int D = a.D;
     full_tables_kernel<T><<<dim3((D + 255) / 256 > 8 ? 8 : (D + 255) / 256, D), 256, 0, st>>>(A, u, D, (T*)Ls, (T*)us);
     cudaError_t e = cudaGetLastError();
@@ -327,8 +314,11 @@ cudaError_t launch_full_genz_t(const double* A, const double* u, const FullArgs&
         }
     }
     const int blocks = a.S * a.blocks_per_shift;
+    if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
     full_genz_kernel<T><<<blocks, kFullP, smem, st>>>((const T*)Ls, (const T*)us, a, (T*)Y, part);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev_end) e = cudaEventRecord(ev_end, st);
+    return e;
 }
 
 }  // namespace
@@ -351,49 +341,51 @@ cudaError_t launch_cov_chol(const double* sites, int64_t D, const vecchia_cov& c
     return e;
 }
 
+int64_t full_genz_blocks_per_shift(int64_t N, bool mixed) {
+    return mixed ? full_tc_blocks_per_shift(N) : (N + kFullP - 1) / kFullP;
+}
+
+// Scratch: the shared part (factor, lattice and shift tables, block sums,
+// status words) followed by the precision's own tables and y history.
 size_t full_genz_scratch_bytes(int64_t D, int64_t N, int S, bool mixed) {
-    const size_t el = mixed ? 4 : 8;
-    const int64_t bps = (N + kFullP - 1) / kFullP;
+    const int64_t bps = (N + kFullP - 1) / kFullP, nblk = full_genz_blocks_per_shift(N, mixed);
     const int64_t dim = D > 1 ? D - 1 : 1;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    return al(sizeof(double) * D * D) + al(el * D * D) + al(el * D) + al(sizeof(uint32_t) * dim * 2) +
-           al(sizeof(double) * S * dim) + al(sizeof(uint32_t) * S * dim) + al(el * (size_t)S * bps * D * kFullP) +
-           al(sizeof(double) * S * bps) + al(sizeof(int)) + al(sizeof(uint64_t) + 2 * sizeof(int64_t) + sizeof(int32_t));
+    const size_t shared = al(sizeof(double) * D * D) + al(sizeof(uint32_t) * dim * 2) + al(sizeof(double) * S * dim) +
+                          al(sizeof(uint32_t) * S * dim) + al(sizeof(double) * S * nblk) + al(2 * sizeof(int)) +
+                          al(sizeof(uint64_t) + 2 * sizeof(int64_t) + sizeof(int32_t));
+    if (mixed) return shared + full_tc_scratch_bytes(D, N, S);
+    return shared + al(sizeof(double) * D * D) + al(sizeof(double) * D) + al(sizeof(double) * (size_t)S * bps * D * kFullP);
 }
 
 cudaError_t launch_full_genz(const double* sites, const double* u, int64_t D, const vecchia_cov& cov, int64_t N,
                              int S, bool mixed, const uint32_t* g_host, const uint32_t* gfix_host,
-                             uint64_t seed, void* scratch, double* part_host, int* bad_host, cudaStream_t st) {
+                             uint64_t seed, void* scratch, double* part_host, int* bad_host, int* timeout_host,
+                             cudaEvent_t ev_begin, cudaEvent_t ev_end, cudaStream_t st) {
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t el = mixed ? 4 : 8;
-    const int64_t bps = (N + kFullP - 1) / kFullP;
+    const int64_t bps = (N + kFullP - 1) / kFullP, nblk = full_genz_blocks_per_shift(N, mixed);
     const int64_t dim = D > 1 ? D - 1 : 1;
     char* p = (char*)scratch;
     double* A = (double*)p;
     p += al(sizeof(double) * D * D);
-    void* Ls = p;
-    p += al(el * D * D);
-    void* us = p;
-    p += al(el * D);
     uint32_t* gdev = (uint32_t*)p;
     p += al(sizeof(uint32_t) * dim * 2);
     double* delta = (double*)p;
     p += al(sizeof(double) * S * dim);
     uint32_t* dfix = (uint32_t*)p;
     p += al(sizeof(uint32_t) * S * dim);
-    void* Y = p;
-    p += al(el * (size_t)S * bps * D * kFullP);
     double* part = (double*)p;
-    p += al(sizeof(double) * S * bps);
-    int* bad = (int*)p;
-    p += al(sizeof(int));
+    p += al(sizeof(double) * S * nblk);
+    int* bad = (int*)p;  // bad[0]: first failing pivot; bad[1]: a device wait timed out
+    p += al(2 * sizeof(int));
     char* small = p;  // seed, offset, S for the shift kernel
+    p += al(sizeof(uint64_t) + 2 * sizeof(int64_t) + sizeof(int32_t));
     uint64_t* seed_d = (uint64_t*)small;
     int64_t* off_d = (int64_t*)(small + sizeof(uint64_t));
     int32_t* S_d = (int32_t*)(small + sizeof(uint64_t) + 2 * sizeof(int64_t));
 
-    const int badinit = INT_MAX;
-    cudaError_t e = cudaMemcpyAsync(bad, &badinit, sizeof(int), cudaMemcpyHostToDevice, st);
+    const int status_init[2] = {INT_MAX, 0};
+    cudaError_t e = cudaMemcpyAsync(bad, status_init, sizeof(status_init), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(gdev, g_host, sizeof(uint32_t) * dim, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(gdev + dim, gfix_host, sizeof(uint32_t) * dim, cudaMemcpyHostToDevice, st);
     const int64_t zero = 0;
@@ -406,20 +398,27 @@ cudaError_t launch_full_genz(const double* sites, const double* u, int64_t D, co
     if (e != cudaSuccess) return e;
     e = launch_cov_chol(sites, D, cov, A, bad, st);
     if (e != cudaSuccess) return e;
-    FullArgs fa;
-    fa.D = (int)D;
-    fa.N = N;
-    fa.S = S;
-    fa.blocks_per_shift = (int)bps;
-    fa.g = gdev;
-    fa.gfix = gdev + dim;
-    fa.delta = delta;
-    fa.dfix = dfix;
-    fa.dim = (int)dim;
-    e = mixed ? launch_full_genz_t<float>(A, u, fa, Ls, us, Y, part, st)
-              : launch_full_genz_t<double>(A, u, fa, Ls, us, Y, part, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(part_host, part, sizeof(double) * S * bps, cudaMemcpyDeviceToHost, st);
+    if (mixed) {
+        e = launch_full_genz_tc(A, u, D, N, S, gdev + dim, dfix, (int)dim, p, part, bad + 1, ev_begin, ev_end, st);
+    } else {
+        void* Ls = p;
+        p += al(sizeof(double) * D * D);
+        void* us = p;
+        p += al(sizeof(double) * D);
+        void* Y = p;
+        FullArgs fa;
+        fa.D = (int)D;
+        fa.N = N;
+        fa.S = S;
+        fa.blocks_per_shift = (int)bps;
+        fa.g = gdev;
+        fa.delta = delta;
+        fa.dim = (int)dim;
+        e = launch_full_genz_t<double>(A, u, fa, Ls, us, Y, part, ev_begin, ev_end, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(part_host, part, sizeof(double) * S * nblk, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(timeout_host, bad + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
     return e;
 }
 

@@ -148,9 +148,22 @@ cudaError_t launch_conditioning(const double* L, int k, const double* sites_i, c
 // Cholesky, Genz over all variables; part_host gets S x ceil(N/128) tile sums
 // of the point products, *bad_host the first non-positive pivot (INT_MAX if none).
 size_t full_genz_scratch_bytes(int64_t D, int64_t N, int S, bool mixed);
+// Point-block sums per shift written by launch_full_genz.
+int64_t full_genz_blocks_per_shift(int64_t N, bool mixed);
+// part_host: per-shift point-block sums (S x full_genz_blocks_per_shift); bad_host:
+// the first failing pivot (INT_MAX if none); timeout_host: nonzero if a device
+// wait of the tensor-core kernel ran out; ev_begin / ev_end (may be null) are
+// recorded around the recursion kernel alone.
 cudaError_t launch_full_genz(const double* sites, const double* u, int64_t D, const vecchia_cov& cov, int64_t N,
                              int S, bool mixed, const uint32_t* g_host, const uint32_t* gfix_host,
-                             uint64_t seed, void* scratch, double* part_host, int* bad_host, cudaStream_t st);
+                             uint64_t seed, void* scratch, double* part_host, int* bad_host, int* timeout_host,
+                             cudaEvent_t ev_begin, cudaEvent_t ev_end, cudaStream_t st);
+// The mixed recursion on the tensor cores (full_tc.cu), given the FP64 factor A.
+size_t full_tc_scratch_bytes(int64_t D, int64_t N, int S);
+int64_t full_tc_blocks_per_shift(int64_t N);
+cudaError_t launch_full_genz_tc(const double* A, const double* u, int64_t D, int64_t N, int S, const uint32_t* gfix,
+                                const uint32_t* dfix, int dim, void* scratch, double* part, int* timeout,
+                                cudaEvent_t ev_begin, cudaEvent_t ev_end, cudaStream_t st);
 
 // sites_out[k] = sites[perm[k]], u_out[k] = u[perm[k]]; *bad = 1 on an index out of range.
 cudaError_t launch_gather(const int32_t* perm, const double* sites, const double* u, int64_t D,
