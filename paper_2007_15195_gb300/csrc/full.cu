@@ -117,13 +117,22 @@ __global__ void chol_trsm_kernel(double* __restrict__ A, int D, int k0) {
 }
 
 // Trailing update of the lower triangle below block column k0: 32 x 32 tiles
-// (tile rows >= tile columns), 256 threads, 4 entries each.
-__global__ void chol_update_kernel(double* __restrict__ A, int D, int k0) {
+// (tile rows >= tile columns), 256 threads, 4 entries each.  part 0: the first
+// tile column (the next block column), one CTA per tile row; part 1: the tile
+// columns after it.
+__global__ void chol_update_kernel(double* __restrict__ A, int D, int k0, int part) {
     __shared__ double Lr[kCholB][kCholB + 1], Lc[kCholB][kCholB + 1];
     const int base = k0 + kCholB;
     // tile pair (tr, tc), tc <= tr, from the linear block index
     int tr, tc;
-    tri_rc(blockIdx.x, tr, tc);
+    if (part == 0) {
+        tr = blockIdx.x;
+        tc = 0;
+    } else {
+        tri_rc(blockIdx.x, tr, tc);
+        ++tr;
+        ++tc;
+    }
     const int r0 = base + tr * kCholB, c0 = base + tc * kCholB;
     for (int x = threadIdx.x; x < kCholB * kCholB; x += blockDim.x) {
         const int i = x / kCholB, t = x % kCholB;
@@ -323,21 +332,73 @@ cudaError_t launch_full_genz_t(const double* A, const double* u, const FullArgs&
 
 }  // namespace
 
+// Blocked Cholesky with a one-block lookahead on two streams.  The caller's
+// stream st carries the critical path: update of block column k by step k-1,
+// then its diagonal factor and the rows below it; a second stream applies the
+// rest of step k's trailing update meanwhile.  Every entry still receives the
+// steps' terms in ascending order: the rest of step k-1 finishes before the
+// first-column update of step k, and each stream keeps its own order.
 cudaError_t launch_cov_chol(const double* sites, int64_t D, const vecchia_cov& cov, double* A, int* bad,
                             cudaStream_t st) {
     if (D <= 0) return cudaSuccess;
     full_cov_kernel<<<dim3((unsigned)((D + 127) / 128), (unsigned)D), 128, 0, st>>>(sites, (int)D, cov_params(cov), A);
     cudaError_t e = cudaGetLastError();
-    for (int64_t k0 = 0; k0 < D && e == cudaSuccess; k0 += kCholB) {
-        chol_diag_kernel<<<1, 32, 0, st>>>(A, (int)D, (int)k0, bad);
-        const int64_t rows = D - k0 - kCholB;
-        if (rows > 0) {
-            chol_trsm_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(A, (int)D, (int)k0);
-            const int64_t tiles = (rows + kCholB - 1) / kCholB;
-            chol_update_kernel<<<(unsigned)(tiles * (tiles + 1) / 2), 256, 0, st>>>(A, (int)D, (int)k0);
+    const int64_t nblk = (D + kCholB - 1) / kCholB;
+    if (nblk <= 2 || e != cudaSuccess) {  // nothing to overlap
+        for (int64_t k0 = 0; k0 < D && e == cudaSuccess; k0 += kCholB) {
+            chol_diag_kernel<<<1, 32, 0, st>>>(A, (int)D, (int)k0, bad);
+            const int64_t rows = D - k0 - kCholB;
+            if (rows > 0) {
+                chol_trsm_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(A, (int)D, (int)k0);
+                chol_update_kernel<<<1, 256, 0, st>>>(A, (int)D, (int)k0, 0);
+            }
+            e = cudaGetLastError();
         }
-        e = cudaGetLastError();
+        return e;
     }
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_panel = nullptr, ev_rest[2] = {nullptr, nullptr};
+    e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_rest[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_rest[1], cudaEventDisableTiming);
+    for (int64_t k = 0; k < nblk && e == cudaSuccess; ++k) {
+        const int64_t k0 = k * kCholB, rows = D - k0 - kCholB;
+        chol_diag_kernel<<<1, 32, 0, st>>>(A, (int)D, (int)k0, bad);
+        if (rows <= 0) {
+            e = cudaGetLastError();
+            break;
+        }
+        chol_trsm_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(A, (int)D, (int)k0);
+        const int64_t tiles = (rows + kCholB - 1) / kCholB;
+        if (tiles > 1) {  // the rest of step k on the side stream
+            if (e == cudaSuccess) e = cudaEventRecord(ev_panel, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_panel, 0);
+            if (e == cudaSuccess) {
+                chol_update_kernel<<<(unsigned)(tiles * (tiles - 1) / 2), 256, 0, side>>>(A, (int)D, (int)k0, 1);
+                e = cudaEventRecord(ev_rest[k & 1], side);
+            }
+        }
+        // the first column of step k needs the rest of step k - 1
+        if (k > 0 && e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_rest[(k - 1) & 1], 0);
+        if (e == cudaSuccess) {
+            chol_update_kernel<<<(unsigned)tiles, 256, 0, st>>>(A, (int)D, (int)k0, 0);
+            e = cudaGetLastError();
+        }
+    }
+    // the last rest update joins the caller's stream
+    if (e == cudaSuccess) {
+        const int64_t last = nblk - 2;  // the last step with a trailing matrix of more than one tile
+        for (int64_t k = last; k >= 0; --k)
+            if ((D - k * kCholB - kCholB + kCholB - 1) / kCholB > 1) {
+                e = cudaStreamWaitEvent(st, ev_rest[k & 1], 0);
+                break;
+            }
+    }
+    if (ev_panel) cudaEventDestroy(ev_panel);
+    if (ev_rest[0]) cudaEventDestroy(ev_rest[0]);
+    if (ev_rest[1]) cudaEventDestroy(ev_rest[1]);
+    if (side) cudaStreamDestroy(side);
     return e;
 }
 
