@@ -69,8 +69,9 @@ ALG_OPS_STEP = 34
 GENZ_TRAFFIC_BYTES_M20 = 364_032
 # DRAM bytes of one launch of the full-Genz recursion kernel on the tensor
 # cores (full_genz_tc_kernel, 50x50 grid, D = 2,500, N = 4,096 x S = 16), from
-# one ncu capture of that launch: 26.79 GB read + 1.66 GB written.
-FULL_TC_TRAFFIC_BYTES_D2500 = 28_442_826_000
+# one ncu capture of that launch (read + written); None until taken for the
+# kernel as it stands.
+FULL_TC_TRAFFIC_BYTES_D2500 = None
 FULL_TC_POINTS, FULL_TC_PANEL, FULL_TC_CHUNK = 224, 64, 16
 
 
@@ -84,16 +85,17 @@ def hbm_peak_gbs():
 
 
 def full_tc_bytes(D, N, S):
-    """DRAM bytes the tensor-core full-Genz kernel moves by design: every panel
-    of 64 variables re-reads the y history of its tile (hi and lo, 224 rows of
-    each 16-variable chunk) below the panel, and each chunk is written once."""
+    """DRAM bytes the tensor-core full-Genz kernel moves by design: panels go in
+    pairs (b, b + 1), b = 2q; pair q re-reads the 4b history chunks of its tile
+    below panel b once (hi and lo, 224 rows of each 16-variable chunk) and the
+    four chunks of panel b's own y; each chunk is written once."""
     Dp = -(-D // FULL_TC_PANEL) * FULL_TC_PANEL
     n_p = Dp // FULL_TC_PANEL
+    per_panel = FULL_TC_PANEL // FULL_TC_CHUNK
     tiles = S * -(-N // FULL_TC_POINTS)
     chunk = 2 * FULL_TC_POINTS * FULL_TC_CHUNK * 4
-    reads = tiles * (FULL_TC_PANEL // FULL_TC_CHUNK) * n_p * (n_p - 1) // 2 * chunk
-    writes = tiles * (Dp // FULL_TC_CHUNK) * chunk
-    return reads + writes
+    loads = sum(per_panel * 2 * q + (per_panel if 2 * q + 1 < n_p else 0) for q in range((n_p + 1) // 2))
+    return tiles * (loads + Dp // FULL_TC_CHUNK) * chunk
 
 
 def parse():
@@ -378,7 +380,8 @@ def run_ours(args):
             "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "traffic": FULL_TC_TRAFFIC_BYTES_D2500 if (D == 2500 and N * S == 65536) else None,
             "kernel": "full_genz_tc_kernel", "peak_source": src,
-            "bytes": "y history re-read per panel of 64 variables (hi and lo) + written once: %d per launch" % nbytes,
+            "bytes": "y history re-read once per pair of 64-variable panels (hi and lo) + written once: %d per launch"
+                     % nbytes,
             "contraction_tflops": float(N) * S * D * (D - 1) / t_k / 1e12,
             "contraction_note": "the conditional-mean products of all D(D-1)/2 pairs, counted as FP32 FMAs "
                                 "(2 flops); the tensor cores run each as three TF32 products"}

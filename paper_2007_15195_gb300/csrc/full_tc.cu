@@ -16,16 +16,20 @@
 // Roles (256 threads: seven point warps and one copy/MMA warp, so that two
 // CTAs per SM leave four warps and 128 registers a thread on each SMSP):
 //   warp 7 lane 0 streams history chunks (16 variables x 224 points, hi and lo,
-//     28 KB) and the matching blocks of L (64 x 16, hi and lo, 8 KB) through a
-//     two-stage shared-memory ring with cp.async.bulk, and issues the MMAs
-//     (12 per chunk); the chunks holding the previous panel's y wait until the
-//     point threads have written them;
+//     28 KB) and the matching blocks of L (64 x 16, hi and lo, 8 KB each)
+//     through a two-stage shared-memory ring with cp.async.bulk and issues the
+//     MMAs.  Panels go in pairs (b, b + 1): one pass over the history chunks
+//     below panel b feeds both panels' accumulators (24 MMAs a chunk), so the
+//     history is read once per pair; the four chunks of panel b's own y then
+//     complete panel b + 1.  A chunk is loaded only after the point threads
+//     have written it;
 //   warps 0..6, one thread per point, run each panel's variables in order from
 //     the accumulator: the in-panel terms (FP32 fma, right-looking), Phi, the
 //     running product in FP64, Phi^{-1} of the lattice-weighted probability;
 //     y goes to the history (hi, lo) in the MMA operand layout.
-// Two accumulator buffers let the MMAs of panel b+1 over the history before
-// panel b run while panel b's variables are processed.  Every wait is bounded
+// The two accumulators of a pair fill the CTA's 256 tensor-memory columns; the
+// next pair's MMAs start once panel b + 1's accumulator has been read out, so
+// they run while panel b + 1's variables are processed.  Every wait is bounded
 // by the global timer; on expiry the kernel records a timeout, waits (bounded)
 // for its copies and MMAs in flight, frees its tensor memory and returns.
 //
@@ -54,10 +58,12 @@ constexpr int kTcThreads = kTcPoints + 32;      // point warps + the copy/MMA wa
 constexpr uint32_t kChunkA = 2 * kTcHalf * kTcKC * 4 * 2;  // 32 KB: y hi, y lo (256 rows)
 constexpr uint32_t kRowsA = kTcPoints * kTcKC * 4;          // 14 KB: the used rows of hi (or lo)
 constexpr uint32_t kChunkB = kTcB * kTcKC * 4 * 2;       // 8 KB: L hi, L lo
-constexpr uint32_t kStageBytes = kChunkA + kChunkB;
+constexpr uint32_t kStageA = 2 * kRowsA;                    // 28 KB: y hi, then y lo (224 rows each)
+constexpr uint32_t kStageBytes = kStageA + 2 * kChunkB;      // + the L blocks of a pair's two panels
 constexpr uint32_t kLpBytes = kTcB * kTcB * 4;           // the panel's own triangle
-constexpr uint32_t kTcSmem = kTcStages * kStageBytes + kLpBytes;
-constexpr uint32_t kTmemCols = 2 * 2 * kTcB;             // 2 buffers x 2 row blocks x 64
+constexpr uint32_t kPanBytes = 3 * kTcB * 4;                 // the panel's us, g, Delta_s (one shift per CTA)
+constexpr uint32_t kTcSmem = kTcStages * kStageBytes + kLpBytes + kPanBytes;
+constexpr uint32_t kTmemCols = 2 * 2 * kTcB;             // 2 panels x 2 row blocks x 64
 constexpr uint64_t kWaitNs = 2000000000ull;              // 2 s without progress
 
 // instruction descriptor: D F32, A and B TF32, both K-major, N = 64, M = 128
@@ -83,6 +89,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Non-blocking test of the phase of the given parity (for a thread that polls
+// several barriers in turn).
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(smem_u32(b)), "r"(parity)
         : "memory");
@@ -216,6 +233,19 @@ __device__ __noinline__ float2 tc_phi_y(float z, uint32_t X, bool want_y) {
     return make_float2(e, y);
 }
 
+// Jobs (history chunks) of pair q = panels 2q and 2q + 1 of nP.
+__device__ __forceinline__ int pair_jobs(int q, int nP) {
+    const int b = 2 * q;
+    return 4 * b + (b + 1 < nP ? 4 : 0);
+}
+// Move a (pair, job) cursor past finished pairs.
+__device__ __forceinline__ void skip_empty_pairs(int& q, int& c, int nQ, int nP) {
+    while (q < nQ && c >= pair_jobs(q, nP)) {
+        c = 0;
+        ++q;
+    }
+}
+
 // The state one point thread carries through a panel.
 struct PanelState {
     float* z;         // [64] conditional sums of the panel's variables (registers)
@@ -226,6 +256,8 @@ struct PanelState {
     int s;
     float* Yp;        // this point's slot in the history layout
     const float* Lp;  // the panel's triangle, LpT[j][j'] (shared memory)
+    const float* us;  // the panel's u_v / L_vv (shared memory)
+    const uint32_t* gd;  // the panel's lattice g (64 entries), then the CTA's shift (64)
 };
 
 // Variable J of the panel: e and y, the in-panel terms of the later variables
@@ -235,8 +267,8 @@ __device__ __forceinline__ void panel_step(const TcArgs& a, PanelState& ps) {
     if (J >= ps.nb) return;
     const int v = ps.v0 + J;
     const bool want_y = v < a.D - 1;
-    const uint32_t X = want_y ? ps.k * __ldg(a.gfix + v) + __ldg(a.dfix + (int64_t)ps.s * a.dim + v) : 0u;
-    const float2 ey = tc_phi_y(__fsub_rn(__ldg(a.us + v), ps.z[J]), X, want_y);
+    const uint32_t X = ps.k * ps.gd[J] + ps.gd[kTcB + J];
+    const float2 ey = tc_phi_y(__fsub_rn(ps.us[J], ps.z[J]), X, want_y);
     ps.f *= (double)ey.x;
     const float y = ey.y, hi = tf32_round(y);
     ps.yh[J % 4] = hi;
@@ -257,11 +289,13 @@ __device__ __forceinline__ void panel_steps(const TcArgs& a, PanelState& ps, std
 
 __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_empty[kTcStages], bar_acc[2], bar_ydone;
+    __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_empty[kTcStages], bar_acc[2], bar_ydone, bar_tfree;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ double red[kTcPoints / 32];
     float* sLp = (float*)(tc_smem + kTcStages * kStageBytes);
+    float* sUs = sLp + kTcB * kTcB;               // [64] us of the panel
+    uint32_t* sGD = (uint32_t*)(sUs + kTcB);      // [64] g, [64] Delta of this CTA's shift
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x, s = tile / a.tps, tile_in_shift = tile % a.tps;
     float* Yt = a.Y + (int64_t)tile * a.nC * (kChunkA / 4);
@@ -280,6 +314,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
         mbar_init(&bar_acc[0], 1);
         mbar_init(&bar_acc[1], 1);
         mbar_init(&bar_ydone, kTcPoints);
+        mbar_init(&bar_tfree, kTcPoints);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -291,85 +326,115 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
 
     if (warp == 7) {
         if (lane == 0) {
-            // ---- copies and MMAs: chunks (b, c), b = 1 .. nP-1, c < 4 b ----
-            const int total = 2 * nP * (nP - 1);
-            int il = 0, lb = 1, lc = 0;  // next load
-            int im = 0, mb = 1, mc = 0;  // next MMA
-            int seen = 0;                // panels whose y the point threads have written
+            // ---- copies and MMAs, pair by pair: pair q = panels b = 2q and b + 1 ----
+            // job c of a pair is history chunk c: chunks c < 4b feed both panels
+            // (shared), chunks 4b .. 4b+3 (panel b's y) only panel b + 1 (own)
+            const int nQ = (nP + 1) / 2;
+            int total = 0;
+            for (int q = 0; q < nQ; ++q) total += pair_jobs(q, nP);
+            int il = 0, lq = 0, lc = 0;  // next load: pair, job
+            int im = 0, mq = 0, mc = 0;  // next MMA
+            skip_empty_pairs(lq, lc, nQ, nP);
+            skip_empty_pairs(mq, mc, nQ, nP);
+            int seen = 0;   // panels whose y the point threads have written
+            int freed = 0;  // pairs whose accumulators the point threads have read
             bool failed = false;
             uint64_t t_idle = 0;
             int spins = 0;
             while (im < total) {
                 bool progress = false;
                 if (il < total && il < im + kTcStages) {
+                    const int b = 2 * lq, c = lc;
+                    const bool shared = c < 4 * b, has2 = b + 1 < nP;
                     bool gate = true;
-                    if (lc >= 4 * (lb - 1) && seen < lb) {
-                        if (mbar_try(&bar_ydone, (uint32_t)((lb - 1) & 1)))
-                            seen = lb;
-                        else
-                            gate = false;
+                    if (seen <= c / 4) {  // chunk c holds panel c / 4's y
+                        if (mbar_test(&bar_ydone, (uint32_t)(seen & 1))) ++seen;
+                        gate = seen > c / 4;
                     }
                     const int st = il % kTcStages;
                     const uint32_t par = (uint32_t)(((il / kTcStages) & 1) ^ 1);
-                    if (gate && mbar_try(&bar_empty[st], par)) {
+                    if (gate && mbar_test(&bar_empty[st], par)) {
                         unsigned char* sA = tc_smem + st * kStageBytes;
-                        const float* ysrc = Yt + (int64_t)lc * (kChunkA / 4);
-                        mbar_expect_tx(&bar_full[st], 2 * kRowsA + kChunkB);
+                        const float* ysrc = Yt + (int64_t)c * (kChunkA / 4);
+                        const uint32_t nl = (shared && has2) ? 2u : 1u;
+                        mbar_expect_tx(&bar_full[st], kStageA + nl * kChunkB);
                         bulk_g2s(sA, ysrc, kRowsA, &bar_full[st]);
-                        bulk_g2s(sA + kChunkA / 2, ysrc + kChunkA / 8, kRowsA, &bar_full[st]);
-                        bulk_g2s(sA + kChunkA, a.Lb + ((int64_t)lb * a.nC + lc) * (kChunkB / 4), kChunkB,
-                                 &bar_full[st]);
+                        bulk_g2s(sA + kRowsA, ysrc + kChunkA / 8, kRowsA, &bar_full[st]);
+                        if (shared)
+                            bulk_g2s(sA + kStageA, a.Lb + ((int64_t)b * a.nC + c) * (kChunkB / 4), kChunkB,
+                                     &bar_full[st]);
+                        if (has2)
+                            bulk_g2s(sA + kStageA + kChunkB, a.Lb + ((int64_t)(b + 1) * a.nC + c) * (kChunkB / 4),
+                                     kChunkB, &bar_full[st]);
                         ++il;
-                        if (++lc == 4 * lb) {
-                            lc = 0;
-                            ++lb;
-                        }
+                        ++lc;
+                        skip_empty_pairs(lq, lc, nQ, nP);
                         progress = true;
                     }
                 }
                 if (im < il) {
+                    const int b = 2 * mq, c = mc;
+                    const bool shared = c < 4 * b, has2 = b + 1 < nP;
+                    bool gate = true;
+                    if (mq >= 1 && freed < mq) {  // the previous pair's accumulators read out
+                        if (mbar_test(&bar_tfree, (uint32_t)((mq - 1) & 1)))
+                            freed = mq;
+                        else
+                            gate = false;
+                    }
                     const int st = im % kTcStages;
-                    if (mbar_try(&bar_full[st], (uint32_t)((im / kTcStages) & 1))) {
+                    if (gate && mbar_test(&bar_full[st], (uint32_t)((im / kTcStages) & 1))) {
                         tc_fence_after();
-                        const uint32_t sA = smem_u32(tc_smem + st * kStageBytes), sB = sA + kChunkA;
-                        const uint32_t dbuf = tmem + (uint32_t)((mb & 1) * 2 * kTcB);
+                        const uint32_t sA = smem_u32(tc_smem + st * kStageBytes);
+                        const uint32_t sB0 = sA + kStageA, sB1 = sB0 + kChunkB;
 #pragma unroll
                         for (int ks = 0; ks < kTcKC / 8; ++ks) {
-                            const uint64_t bh = sdesc(sB + ks * 256), bl = sdesc(sB + kChunkB / 2 + ks * 256);
+                            const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 const uint64_t ah = sdesc(sA + h * (kChunkA / 4) + ks * 256);
-                                const uint64_t al = sdesc(sA + kChunkA / 2 + h * (kChunkA / 4) + ks * 256);
-                                const uint32_t d = dbuf + (uint32_t)(h * kTcB);
-                                mma_tf32(d, ah, bh, (mc > 0 || ks > 0) ? 1u : 0u);
-                                mma_tf32(d, ah, bl, 1u);
-                                mma_tf32(d, al, bh, 1u);
+                                const uint64_t al = sdesc(sA + kRowsA + h * (kChunkA / 4) + ks * 256);
+                                if (shared) {
+                                    const uint32_t d = tmem + (uint32_t)(h * kTcB);
+                                    const uint64_t bh = sdesc(sB0 + ks * 256), bl = sdesc(sB0 + kChunkB / 2 + ks * 256);
+                                    mma_tf32(d, ah, bh, acc);
+                                    mma_tf32(d, ah, bl, 1u);
+                                    mma_tf32(d, al, bh, 1u);
+                                }
+                                if (has2) {
+                                    const uint32_t d = tmem + (uint32_t)(2 * kTcB + h * kTcB);
+                                    const uint64_t bh = sdesc(sB1 + ks * 256), bl = sdesc(sB1 + kChunkB / 2 + ks * 256);
+                                    mma_tf32(d, ah, bh, acc);
+                                    mma_tf32(d, ah, bl, 1u);
+                                    mma_tf32(d, al, bh, 1u);
+                                }
                             }
                         }
                         mma_commit(&bar_empty[st]);
-                        if (mc == 4 * mb - 1) mma_commit(&bar_acc[mb & 1]);
+                        if (shared && c == 4 * b - 1) mma_commit(&bar_acc[0]);
+                        if (!shared && c == 4 * b + 3) mma_commit(&bar_acc[1]);
                         ++im;
-                        if (++mc == 4 * mb) {
-                            mc = 0;
-                            ++mb;
-                        }
+                        ++mc;
+                        skip_empty_pairs(mq, mc, nQ, nP);
                         progress = true;
                     }
                 }
                 if (progress) {
                     spins = 0;
-                } else if (++spins == 64) {
-                    spins = 0;
-                    const uint64_t now = global_ns();
-                    if (t_idle == 0) {
-                        t_idle = now;
-                    } else if (now - t_idle > kWaitNs || *(volatile int*)&abort_flag) {
-                        failed = true;
-                        break;
+                    t_idle = 0;
+                } else {
+                    __nanosleep(32);  // leave the issue slots to the point warps
+                    if (++spins == 64) {
+                        spins = 0;
+                        const uint64_t now = global_ns();
+                        if (t_idle == 0) {
+                            t_idle = now;
+                        } else if (now - t_idle > kWaitNs || *(volatile int*)&abort_flag) {
+                            failed = true;
+                            break;
+                        }
                     }
-                    continue;
                 }
-                if (progress) t_idle = 0;
             }
             if (failed) {
                 atomicExch(&abort_flag, 1);
@@ -392,7 +457,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
         for (int b = 0; b < nP; ++b) {
             const int v0 = b * kTcB, nb = min(kTcB, a.D - v0);
             bool ok = true;
-            if (b > 0) ok = mbar_wait(&bar_acc[b & 1], (uint32_t)(((b - 1) >> 1) & 1));
+            // panel 2q: the shared chunks of pair q (q >= 1); panel 2q + 1: its own chunks too
+            if (b > 0)
+                ok = (b & 1) ? mbar_wait(&bar_acc[1], (uint32_t)((b >> 1) & 1))
+                             : mbar_wait(&bar_acc[0], (uint32_t)(((b >> 1) - 1) & 1));
             if (points_any(!ok || *(volatile int*)&abort_flag)) {
                 if (p == 0) {
                     atomicExch(&abort_flag, 1);
@@ -403,6 +471,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
             {
                 const float4* src = (const float4*)(a.LpT + (int64_t)b * kTcB * kTcB);
                 for (int i = p; i < kTcB * kTcB / 4; i += kTcPoints) ((float4*)sLp)[i] = __ldg(src + i);
+                if (p < kTcB) {
+                    sUs[p] = __ldg(a.us + v0 + p);  // padded to a multiple of 64
+                } else if (p < 3 * kTcB) {
+                    const int j = (p - kTcB) % kTcB, v = v0 + j;  // g and Delta exist for v < D - 1
+                    sGD[p - kTcB] = (v < a.dim) ? (p < 2 * kTcB ? __ldg(a.gfix + v) : __ldg(a.dfix + (int64_t)s * a.dim + v))
+                                                : 0u;
+                }
             }
             float z[kTcB];
             if (b > 0) {
@@ -412,12 +487,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
                 for (int i = 0; i < kTcB / 16; ++i) tmem_ld16(tb + i * 16, z + 16 * i);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 tc_fence_before();
+                if (b & 1) mbar_arrive(&bar_tfree);  // the pair's accumulators may be reused
             } else {
 #pragma unroll
                 for (int i = 0; i < kTcB; ++i) z[i] = 0.0f;
             }
             points_sync();
-            PanelState ps{z, {}, {}, f, nb, v0, k, s, Yp, sLp};
+            PanelState ps{z, {}, {}, f, nb, v0, k, s, Yp, sLp, sUs, sGD};
             panel_steps(a, ps, std::make_integer_sequence<int, kTcB>{});
             f = ps.f;
             asm volatile("fence.proxy.async.global;" ::: "memory");
