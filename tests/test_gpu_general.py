@@ -218,6 +218,21 @@ def test_full_genz_against_oracle(ctx, prec, D, N, S):
         assert se == pytest.approx(ref_se, rel=1e-6)
 
 
+@pytest.mark.parametrize("D,N,S", [(64, 224, 2),    # one full panel, one exact tile of points
+                                   (65, 225, 3),    # two panels (the pair's own chunks only), a ragged tile
+                                   (129, 448, 2),   # three panels: the last pair has one panel
+                                   (256, 100, 4),   # four panels, one partial tile per shift
+                                   (321, 673, 2)])  # five panels, three tiles per shift, ragged
+def test_full_genz_panel_pairs_against_oracle(ctx, D, N, S):
+    """The mixed recursion on the tensor cores takes panels of 64 variables in
+    pairs over tiles of 224 points: panel counts odd and even, tiles exact and
+    ragged."""
+    s, u, cov = _ordered(D, 900 + D, cov=(B.COV_MATERN, 1.0, 0.25, 1.5, 0.0))
+    ref, _ = O.full_genz(s, cov, u, N, S, 7)
+    lp, _ = B.vecchia_full_genz(ctx, s, cov, u, N, S, seed=7, precision=B.MIXED)
+    _check(lp, ref, B.MIXED)
+
+
 @pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
 def test_full_genz_equals_vecchia_with_every_neighbour(ctx, prec):
     """Eq. (vecchia-cdf) with m = D - 1 telescopes to the full estimate."""
