@@ -52,40 +52,47 @@ __device__ __forceinline__ void tri_rc(int e, int& r, int& c) {
     c = e - r * (r + 1) / 2;
 }
 
-// The diagonal block at k0 (one warp): right-looking, trailing updates packed.
-__global__ void chol_diag_kernel(double* __restrict__ A, int D, int k0, int* __restrict__ bad) {
+// The diagonal block at k0 (128 threads): right-looking; at step j the column
+// below the pivot is divided by it, then the packed trailing triangle takes one
+// fma per entry, spread over the threads through a table of (row, column)
+// pairs in packed order (the pairs of an n x n triangle are the table's first
+// n (n + 1) / 2 entries).
+__global__ void __launch_bounds__(128) chol_diag_kernel(double* __restrict__ A, int D, int k0,
+                                                        int* __restrict__ bad) {
     __shared__ double T[kCholB][kCholB + 1];
-    const int lane = threadIdx.x;
+    __shared__ unsigned short tab[kCholB * (kCholB - 1) / 2];
+    const int tid = threadIdx.x;
     const int b = min(kCholB, D - k0);
-    for (int e = lane; e < b * (b + 1) / 2; e += 32) {
+    for (int e = tid; e < b * (b + 1) / 2; e += blockDim.x) {
         int r, c;
         tri_rc(e, r, c);
         T[r][c] = A[(int64_t)(k0 + r) * D + k0 + c];
     }
-    __syncwarp();
-    bool ok = true;
+    for (int e = tid; e < kCholB * (kCholB - 1) / 2; e += blockDim.x) {
+        int r, c;
+        tri_rc(e, r, c);
+        tab[e] = (unsigned short)((r << 8) | c);
+    }
+    __syncthreads();
     for (int j = 0; j < b; ++j) {
         const double s = T[j][j];
-        if (!(s > 0.0)) {  // warp-uniform
-            ok = false;
-            if (lane == 0) atomicMin(bad, k0 + j);
-            break;
+        if (!(s > 0.0)) {  // block-uniform
+            if (tid == 0) atomicMin(bad, k0 + j);
+            return;
         }
         const double piv = sqrt(s);
-        for (int r = j + 1 + lane; r < b; r += 32) T[r][j] = T[r][j] / piv;
-        __syncwarp();
-        if (lane == 0) T[j][j] = piv;
+        if (tid < b - 1 - j) T[j + 1 + tid][j] = T[j + 1 + tid][j] / piv;
+        __syncthreads();
+        if (tid == 0) T[j][j] = piv;
         const int n = b - 1 - j;
-        for (int e = lane; e < n * (n + 1) / 2; e += 32) {
-            int a, c;
-            tri_rc(e, a, c);
-            const int r = j + 1 + a, cc = j + 1 + c;
+        for (int e = tid; e < n * (n + 1) / 2; e += blockDim.x) {
+            const unsigned t = tab[e];
+            const int r = j + 1 + (int)(t >> 8), cc = j + 1 + (int)(t & 255u);
             T[r][cc] = fma(-T[r][j], T[cc][j], T[r][cc]);
         }
-        __syncwarp();
+        __syncthreads();
     }
-    if (!ok) return;
-    for (int e = lane; e < b * (b + 1) / 2; e += 32) {
+    for (int e = tid; e < b * (b + 1) / 2; e += blockDim.x) {
         int r, c;
         tri_rc(e, r, c);
         A[(int64_t)(k0 + r) * D + k0 + c] = T[r][c];
@@ -346,7 +353,7 @@ cudaError_t launch_cov_chol(const double* sites, int64_t D, const vecchia_cov& c
     const int64_t nblk = (D + kCholB - 1) / kCholB;
     if (nblk <= 2 || e != cudaSuccess) {  // nothing to overlap
         for (int64_t k0 = 0; k0 < D && e == cudaSuccess; k0 += kCholB) {
-            chol_diag_kernel<<<1, 32, 0, st>>>(A, (int)D, (int)k0, bad);
+            chol_diag_kernel<<<1, 128, 0, st>>>(A, (int)D, (int)k0, bad);
             const int64_t rows = D - k0 - kCholB;
             if (rows > 0) {
                 chol_trsm_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(A, (int)D, (int)k0);
@@ -364,7 +371,7 @@ cudaError_t launch_cov_chol(const double* sites, int64_t D, const vecchia_cov& c
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_rest[1], cudaEventDisableTiming);
     for (int64_t k = 0; k < nblk && e == cudaSuccess; ++k) {
         const int64_t k0 = k * kCholB, rows = D - k0 - kCholB;
-        chol_diag_kernel<<<1, 32, 0, st>>>(A, (int)D, (int)k0, bad);
+        chol_diag_kernel<<<1, 128, 0, st>>>(A, (int)D, (int)k0, bad);
         if (rows <= 0) {
             e = cudaGetLastError();
             break;
