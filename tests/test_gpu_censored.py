@@ -41,7 +41,8 @@ def _check(got, ref, prec):
 
 
 @pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
-@pytest.mark.parametrize("D,k,m,n_nodes", [(120, 8, 10, 0), (120, 8, 10, 6), (200, 40, 20, 4), (90, 3, 40, 0)])
+@pytest.mark.parametrize("D,k,m,n_nodes", [(120, 8, 10, 0), (120, 8, 10, 6), (200, 40, 20, 4), (90, 3, 40, 0),
+                                            (400, 150, 10, 0)])  # 5 blocks of Sigma_II: the two-stream factor
 def test_censored_against_oracle(ctx, prec, D, k, m, n_nodes):
     sc, xc, si, xi = _split(D, k, 10 + k, m)
     nbr = B.vecchia_neighbors(ctx, sc, m)
