@@ -225,7 +225,7 @@ __device__ __noinline__ float2 tc_phi_y(float z, uint32_t X, bool want_y) {
     special::phi_pair_fast(z, e, ec);
     float y = 0.0f;
     if (want_y) {
-        const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
+        const uint32_t V = ((int32_t)X < 0) ? 0u - X : X;  // tent: w = |int32(X)| 2^-31
         const float w = __fmul_rn(__uint2float_rn(V), 0x1p-31f);
         const float am = __fmul_rn(__uint2float_rn(0x80000000u - V), 0x1p-31f);  // |2x - 1|
         y = special::phiinv_pq(__fmul_rn(w, e), fmaf(w, ec, am));

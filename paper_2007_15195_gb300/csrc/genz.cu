@@ -170,8 +170,9 @@ __device__ __forceinline__ void mixed_steps(const GenzSmem<DMAX, true>& sm, cons
                     scale_by_log2(L.g[p], L.E[p], L.le2[p]);
             }
             // lattice coordinate in 32-bit fixed point, tent transform w = 1 - |2x - 1|
+            // of x = X 2^-32: exactly |int32(X)| 2^-31
             const uint32_t X = L.kk[p] * G + Dt;
-            const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
+            const uint32_t V = ((int32_t)X < 0) ? 0u - X : X;
             const float w = __uint2float_rn(V) * 0x1p-31f;
             float y;
             if (!L.tiny[p]) {
@@ -278,8 +279,7 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
     if constexpr (P == 1) {  // one point per lane: the per-point form keeps fewer values live
         if (!FIRST) g[0] = __fmul_rn(g[0], e[0]);
         const uint32_t X = kk[0] * G + Dt;
-        const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
-        const float w = __fmul_rn(__uint2float_rn(V), 0x1p-31f);
+        const float w = __fmul_rn(fabsf(__int2float_rn((int32_t)X)), 0x1p-31f);  // |int32(X)| 2^-31
         const float yv = special::phiinv_pq(__fmul_rn(w, e[0]), fmaf(w, ec[0], __fsub_rn(1.0f, w)));
         const float z = fmaf(-lz, yv, R[0][0]);
 #pragma unroll
@@ -296,9 +296,9 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
     for (int p = 0; p < P; ++p) {
         if (!FIRST) g[p] = __fmul_rn(g[p], e[p]);  // g = e_1 ... e_t
         // lattice coordinate in 32-bit fixed point, tent transform w = 1 - |2x - 1|
+        // of x = X 2^-32: exactly |int32(X)| 2^-31 (the sign folds into the product)
         const uint32_t X = kk[p] * G + Dt;
-        const uint32_t V = X ^ (uint32_t)((int32_t)X >> 31);
-        const float w = __fmul_rn(__uint2float_rn(V), 0x1p-31f);
+        const float w = __fmul_rn(fabsf(__int2float_rn((int32_t)X)), 0x1p-31f);
         pp[p] = __fmul_rn(w, e[p]);
         qq[p] = fmaf(w, ec[p], __fsub_rn(1.0f, w));
         y[p] = special::phiinv_central(pp[p], qq[p], tail[p]);
