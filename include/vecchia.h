@@ -307,12 +307,15 @@ int vecchia_mixture_log_cdf(vecchia_ctx* ctx, const double* sites_ordered, int64
  * with.  Covariance and Cholesky in FP64 (blocked; each entry of the factor
  * takes its terms in ascending order with fma, then the pivot division);
  * the recursion over all D variables in the precision requested (mixed: FP32
- * integrand and conditional means, FP64 running product and sums).  log_p =
- * log of the mean over shifts of the lattice means; rel_se = their standard
- * error over the mean.  Arrays host or device (both of one kind); device
- * memory grows as 12 D^2 + 4 (8 for FP64) D S N bytes.  D <= VECCHIA_FULL_MAX_D.
- * A non-positive pivot gives VECCHIA_ERR_NOT_PD with its site in
- * vecchia_last_error_site(). */
+ * integrand, conditional means on the tensor cores from TF32 hi/lo splits of
+ * the FP32 operands -- FP32-level accuracy --, FP64 running product and
+ * sums).  log_p = log of the mean over shifts of the lattice means; rel_se =
+ * their standard error over the mean.  Arrays host or device (both of one
+ * kind); device memory grows as about 16 D^2 + 9.2 (mixed) or 8 (FP64) D S N
+ * bytes.  D <= VECCHIA_FULL_MAX_D.  A non-positive pivot gives
+ * VECCHIA_ERR_NOT_PD with its site in vecchia_last_error_site();
+ * VECCHIA_ERR_TIMEOUT means a bounded device wait of the mixed recursion ran
+ * out (2 s without progress). */
 #define VECCHIA_FULL_MAX_D 32768
 int vecchia_full_genz(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, vecchia_cov cov,
                       const double* u, int64_t N, int S, uint64_t seed, int precision, double* log_p,
