@@ -38,7 +38,7 @@
 //     (r / 8) * 512 + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4,
 // so the descriptor's K-direction core-matrix stride is 128 B and its
 // row-group stride 512 B.
-#include <climits>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -161,21 +161,8 @@ __device__ __forceinline__ void points_sync() { asm volatile("bar.sync 1, 224;" 
 
 // x rounded to the nearest TF32 value (ties away from zero): add half a unit of
 // the 13 dropped bits to the magnitude and clear them.
-__host__ __device__ __forceinline__ float tf32_round(float x) {
-#ifdef __CUDA_ARCH__
-    uint32_t u = __float_as_uint(x);
-#else
-    uint32_t u;
-    memcpy(&u, &x, 4);
-#endif
-    u = (u + 0x1000u) & 0xFFFFE000u;
-#ifdef __CUDA_ARCH__
-    return __uint_as_float(u);
-#else
-    float y;
-    memcpy(&y, &u, 4);
-    return y;
-#endif
+__device__ __forceinline__ float tf32_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 struct TcArgs {
