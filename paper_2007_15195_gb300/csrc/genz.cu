@@ -64,8 +64,8 @@ struct GenzSmem {
     //   Lz[t]      = L_{t+1,t}          coefficient of y_t in variable t+1
     //   Lup[t][r]  = L_{t+2+r,t}        coefficients of y_t in the later variables
     // MIXED divides each row v by L_vv (so the conditional mean is already
-    // standardised); FP64 keeps them unscaled and divides by L_vv, as the
-    // row-by-row definition does.
+    // standardised); FP64 keeps them unscaled and multiplies the conditional
+    // mean by 1/L_vv (diag), one rounding more than the definition's division.
     static constexpr int LS = (DMAX + 3) & ~3;  // row stride: 16-byte aligned rows
     __align__(16) T Lup[DMAX][LS];
     __align__(16) T Lz[DMAX];
@@ -400,7 +400,7 @@ __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm
     const int lane = threadIdx.x & 31;
     const double* dl = P.delta + (int64_t)s * P.dim;
     const uint64_t N = (uint64_t)P.N;
-    const double Nd = (double)P.N;
+    const double Nd = (double)P.N, invN = 1.0 / Nd;
     for (int64_t k = k_begin + lane; k < k_end; k += 32) {
         double R[DMAX - 1];
 #pragma unroll
@@ -410,7 +410,7 @@ __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm
             f *= e;  // e_0 ... e_t
             if (t + 1 == c) fc = f;  // the c-dim CDF sample of the leading block
             const uint64_t rr = ((uint64_t)k * (uint64_t)sm.gl[t]) % N;
-            double x = __dadd_rn((double)rr / Nd, dl[t]);
+            double x = __dadd_rn((double)rr * invN, dl[t]);
             if (x >= 1.0) x -= 1.0;
             const double a = fabs(__dsub_rn(__dmul_rn(2.0, x), 1.0));
             const double w = __dsub_rn(1.0, a);
@@ -421,7 +421,7 @@ __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm
             const double acc = fma(-sm.Lz[t], y, R[0]);
 #pragma unroll
             for (int r = 0; r < W; ++r) R[r] = fma(-lup[r], y, R[r + 1]);
-            phi_pair64(acc / sm.diag[t + 1], e, ec);
+            phi_pair64(acc * sm.diag[t + 1], e, ec);
         }
         acc_den += fc;
         acc_num += f * e;
@@ -648,11 +648,11 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
 
         if (!sm.bad) {
             // ---- derived tables for the recursion ----
-            // (mixed: each row scaled by 1/L_vv, one FP64 reciprocal per row)
+            // (one FP64 reciprocal 1/L_vv per row; mixed: each row scaled by it)
             constexpr int LS = GenzSmem<DMAX, MIXED>::LS;
             const int d = q + 1;
             for (int v = threadIdx.x; v < DMAX; v += blockDim.x)
-                sm.diag[v] = (v < d) ? (MIXED ? 1.0 / sm.A[v][v] : sm.A[v][v]) : 0.0;
+                sm.diag[v] = (v < d) ? 1.0 / sm.A[v][v] : 0.0;
             __syncthreads();
             for (int x = threadIdx.x; x < DMAX * LS; x += blockDim.x) {
                 const int t = x / LS, r = x % LS, v = t + 2 + r;
