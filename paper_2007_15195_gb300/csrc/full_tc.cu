@@ -239,8 +239,7 @@ struct PanelState {
     float yh[4], yl[4];
     double f;         // running product
     int nb, v0;
-    uint32_t k;
-    int s;
+    uint32_t k;       // lattice point index
     float* Yp;        // this point's slot in the history layout
     const float* Lp;  // the panel's triangle, LpT[j][j'] (shared memory)
     const float* us;  // the panel's u_v / L_vv (shared memory)
@@ -480,7 +479,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
                 for (int i = 0; i < kTcB; ++i) z[i] = 0.0f;
             }
             points_sync();
-            PanelState ps{z, {}, {}, f, nb, v0, k, s, Yp, sLp, sUs, sGD};
+            PanelState ps{z, {}, {}, f, nb, v0, k, Yp, sLp, sUs, sGD};
             panel_steps(a, ps, std::make_integer_sequence<int, kTcB>{});
             f = ps.f;
             asm volatile("fence.proxy.async.global;" ::: "memory");
