@@ -50,14 +50,33 @@ int scratch_address(int device, unsigned char** out) {
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-bool device_array(const void* p) {
+// True if p is device (or managed) memory that lives on `device`.
+bool device_array(const void* p, int device) {
     cudaPointerAttributes a;
     if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
 }
+
+// Makes `device` current for the call and puts the caller's device back on
+// every return path.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        ok = cudaSetDevice(device) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 bool cov_valid(const vecchia_cov& c) {
     if (!(c.variance > 0.0) || !(c.range > 0.0) || !(c.nugget >= 0.0)) return false;
@@ -84,11 +103,10 @@ extern "C" int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const doub
     if (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) return VECCHIA_ERR_ARG;
     *log_p = NAN;
     *std_err = NAN;
-    if (cudaSetDevice(device) != cudaSuccess) {
-        cudaGetLastError();
-        return VECCHIA_ERR_ARG;
-    }
-    if (!device_array(sites_ordered) || !device_array(u) || (m > 0 && !device_array(nbr)))
+    const DeviceGuard guard(device);
+    if (!guard.ok) return VECCHIA_ERR_ARG;
+    if (!device_array(sites_ordered, device) || !device_array(u, device) ||
+        (m > 0 && !device_array(nbr, device)))
         return VECCHIA_ERR_ARG;
     const cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool mixed = precision == VECCHIA_MIXED;
