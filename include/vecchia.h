@@ -356,7 +356,8 @@ int vecchia_shifts(uint64_t seed, int S, int dim, double* delta);
  * (bucket b holds problems whose largest term has d <= 9, 13, 17, 21, 25,
  * 29, 32, 48, 64 variables for b = 0..8 -- d = m + 1, or m + p for groups of
  * p; -1 = all): warps per CTA (1..16; at most 8 above 32 variables), points
- * per lane per pass (1 or 2; FP64 and blocks above 32 variables use 1),
+ * per lane per pass (1, 2 or 4; 4 applies to blocks of up to 21 variables and
+ * falls back to 2 above; FP64 and blocks above 32 variables use 1),
  * lattice slices per shift spread over a CTA's warps (>= 1), shift groups per
  * term spread over CTAs (1..VECCHIA_MAX_S).  Tiles change only the launch
  * shape; results are identical up to the order of the final FP64 sums. */
@@ -370,12 +371,31 @@ int vecchia_set_timing(vecchia_ctx* ctx, int enable);
 /* Milliseconds between those events in the last call with timing on. */
 int vecchia_genz_time_ms(const vecchia_ctx* ctx, double* ms);
 
+/* Bounded device waits of vecchia_full_genz's tensor-core recursion (mixed
+ * precision; the paper has no counterpart: this is how the library reports a
+ * stalled kernel instead of hanging).  Its point warps wait on mbarriers for
+ * the accumulators and its copy lane for their progress; a wait with no
+ * progress for limit_ns (0 = the built-in 2 s; values above it are clamped
+ * to it) makes the kernel record a timeout, wait (with the full 2 s limit)
+ * for every copy and MMA it has issued, free its tensor memory and return,
+ * and the call then returns VECCHIA_ERR_TIMEOUT.  withhold != 0 is for tests
+ * of that path only: the copy lane issues no copy and no MMA, so the first
+ * accumulator wait runs out with nothing in flight.  The setting stays on the
+ * context until changed; (0, 0) restores the default. */
+int vecchia_set_full_genz_wait(vecchia_ctx* ctx, uint64_t limit_ns, int withhold);
+
 /* Diagnostic: the FP32 special functions of the mixed path on n values (x and
  * out device arrays of float): which = 0: Phi(x); 1: 1 - Phi(x); 2: log2 Phi(x)
  * for x < -9 (NaN otherwise); 3: Phi^{-1}(x), x in (0, 1); 4: Phi^{-1}(2^x) for
  * x < -64.  These are the maps of Genz's separation of variables (Sec. 2.2)
  * in the precision the mixed path evaluates them. */
 int vecchia_eval_special(vecchia_ctx* ctx, int which, const float* x, int64_t n, float* out);
+
+/* Diagnostic: the FP64 special functions of the FP64 path on n values (x and
+ * out device arrays of double): which = 0: Phi(x); 1: 1 - Phi(x) (from the
+ * tail); 2: Phi^{-1}(x) given p = x, q = 1 - x; 3: Phi^{-1}(1 - x) given q = x
+ * (the upper tail, to full precision).  The same maps (Sec. 2.2) in FP64. */
+int vecchia_eval_special64(vecchia_ctx* ctx, int which, const double* x, int64_t n, double* out);
 
 /* Size of the fixed device array that vecchia_log_cdf_noalloc uses as scratch. */
 #define VECCHIA_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -390,17 +410,23 @@ int vecchia_eval_special(vecchia_ctx* ctx, int which, const float* x, int64_t n,
  * VECCHIA_NOALLOC_SCRATCH_BYTES (32 MiB, held by every GPU that loads the
  * library until the process exits) and calls no allocating routine: no
  * cudaMalloc, cudaFree or cudaMallocHost, and no context is needed.
- *   device, cuda_stream: where to run (stream NULL = legacy default stream).
- *   sites_ordered (D x 2), nbr (D x m), u (D): device memory, as for
+ *   device, cuda_stream: where to run (stream NULL = legacy default stream);
+ *   the stream must belong to `device`.  The call makes `device` current
+ *   while it runs and restores the calling thread's current device before it
+ *   returns.
+ *   sites_ordered (D x 2), nbr (D x m), u (D): device memory on `device`
+ *   (memory of another GPU, or host memory, gives VECCHIA_ERR_ARG), as for
  *   vecchia_log_cdf; log_p, std_err: host scalars.
  * A problem whose scratch (about 16 D S + 16 D bytes, plus 8 D per shift group
  * on the mixed path) exceeds the array returns VECCHIA_ERR_UNSUPPORTED.
  * The first call on a device looks up the array's device address (once per
  * device, under a lock); make that first call before any stream capture.
+ * Every call uploads its parameters from the host and synchronises
+ * cuda_stream before it returns.
  * Every call shares the array and clears what must start at zero; calls
  * whose work overlaps on the GPU (other streams or host threads on the same
  * device) race on it and must be serialised by the caller.  Results equal
- * vecchia_log_cdf's with the built-in tile. */
+ * vecchia_log_cdf's with the built-in tile bit for bit. */
 int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const double* sites_ordered, int64_t D,
                             const int32_t* nbr, int m, vecchia_cov cov, const double* u, int64_t N,
                             int S, uint64_t seed, int precision, double* log_p, double* std_err);

@@ -123,10 +123,12 @@ def lib():
         L.vecchia_reset_tiles.argtypes = [_vp]
         L.vecchia_set_timing.argtypes = [_vp, C.c_int]
         L.vecchia_eval_special.argtypes = [_vp, C.c_int, _vp, C.c_int64, _vp]
+        L.vecchia_eval_special64.argtypes = [_vp, C.c_int, _vp, C.c_int64, _vp]
         L.vecchia_log_cdf_noalloc.argtypes = [C.c_int, _vp, _vp, C.c_int64, _vp, C.c_int, vecchia_cov,
                                               _vp, C.c_int64, C.c_int, C.c_uint64, C.c_int,
                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.vecchia_genz_time_ms.argtypes = [_vp, C.POINTER(C.c_double)]
+        L.vecchia_set_full_genz_wait.argtypes = [_vp, C.c_uint64, C.c_int]
         _lib = L
     return _lib
 
@@ -535,8 +537,24 @@ def vecchia_eval_special(ctx, which, x):
     return out
 
 
+def vecchia_eval_special64(ctx, which, x):
+    """FP64 special functions of the FP64 path on a CUDA float64 tensor (diagnostic)."""
+    xx = x.to(torch.float64).contiguous()
+    out = torch.empty_like(xx)
+    _check(lib().vecchia_eval_special64(ctx.handle, int(which), _ptr(xx), xx.numel(), _ptr(out)),
+           "vecchia_eval_special64", ctx)
+    return out
+
+
 def vecchia_set_timing(ctx, enable=True):
     _check(lib().vecchia_set_timing(ctx.handle, 1 if enable else 0), "vecchia_set_timing", ctx)
+
+
+def vecchia_set_full_genz_wait(ctx, limit_ns=0, withhold=False):
+    """Wait limit of the tensor-core full-Genz kernel (0 = built-in 2 s) and
+    the test switch that makes its copy lane issue nothing."""
+    _check(lib().vecchia_set_full_genz_wait(ctx.handle, C.c_uint64(int(limit_ns)), 1 if withhold else 0),
+           "vecchia_set_full_genz_wait", ctx)
 
 
 def vecchia_genz_time_ms(ctx):

@@ -34,6 +34,10 @@ struct vecchia_ctx {
     size_t astage_cap[2] = {0, 0};
     cudaEvent_t astage_ev[2] = {nullptr, nullptr};
     int astage_i = 0;
+    // tensor-core full Genz: limit of its progress waits (0 = built-in) and the
+    // test switch that makes its copy lane issue nothing
+    uint64_t full_wait_ns = 0;
+    int full_withhold = 0;
 };
 
 namespace vk {
@@ -1386,8 +1390,8 @@ int vecchia_full_genz(vecchia_ctx* c, const double* sites, int64_t D, vecchia_co
         e = cudaMemcpyAsync(A + o_u, u, sizeof(double) * D, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = vk::launch_full_genz(sd, ud, D, cov, N, S, mixed, g.data(), gfix.data(), seed, A + o_scr, part.data(),
-                                 &bad, &timed_out, c->timing ? c->ev0 : nullptr, c->timing ? c->ev1 : nullptr,
-                                 c->stream);
+                                 &bad, &timed_out, c->full_wait_ns, c->full_withhold,
+                                 c->timing ? c->ev0 : nullptr, c->timing ? c->ev1 : nullptr, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1884,7 +1888,7 @@ int vecchia_set_tile(vecchia_ctx* c, int precision, int bucket, int warps, int p
     if (!c || (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) || bucket < -1 ||
         bucket >= vk::kNumBuckets)
         return VECCHIA_ERR_ARG;
-    if (warps < 1 || warps > 16 || (points != 1 && points != 2) || slices < 1 ||
+    if (warps < 1 || warps > 16 || (points != 1 && points != 2 && points != 4) || slices < 1 ||
         groups < 1 || groups > VECCHIA_MAX_S)
         return VECCHIA_ERR_ARG;
     const int b0 = bucket < 0 ? 0 : bucket, b1 = bucket < 0 ? vk::kNumBuckets - 1 : bucket;
@@ -1916,6 +1920,20 @@ int vecchia_eval_special(vecchia_ctx* c, int which, const float* x, int64_t n, f
     return VECCHIA_OK;
 }
 
+int vecchia_eval_special64(vecchia_ctx* c, int which, const double* x, int64_t n, double* out) {
+    if (!c || which < 0 || which > 3 || n < 0 || (n > 0 && (!x || !out))) return VECCHIA_ERR_ARG;
+    if (n == 0) return VECCHIA_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    if (!is_device_ptr(x) || !is_device_ptr(out)) return VECCHIA_ERR_ARG;
+    cudaError_t e = vk::launch_eval_special64(which, x, n, out, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    return VECCHIA_OK;
+}
+
 int vecchia_set_timing(vecchia_ctx* c, int enable) {
     if (!c) return VECCHIA_ERR_ARG;
     c->timing = enable != 0;
@@ -1925,6 +1943,13 @@ int vecchia_set_timing(vecchia_ctx* c, int enable) {
 int vecchia_genz_time_ms(const vecchia_ctx* c, double* ms) {
     if (!c || !ms) return VECCHIA_ERR_ARG;
     *ms = c->genz_ms;
+    return VECCHIA_OK;
+}
+
+int vecchia_set_full_genz_wait(vecchia_ctx* c, uint64_t limit_ns, int withhold) {
+    if (!c) return VECCHIA_ERR_ARG;
+    c->full_wait_ns = limit_ns;
+    c->full_withhold = withhold ? 1 : 0;
     return VECCHIA_OK;
 }
 

@@ -429,7 +429,8 @@ size_t full_genz_scratch_bytes(int64_t D, int64_t N, int S, bool mixed) {
 cudaError_t launch_full_genz(const double* sites, const double* u, int64_t D, const vecchia_cov& cov, int64_t N,
                              int S, bool mixed, const uint32_t* g_host, const uint32_t* gfix_host,
                              uint64_t seed, void* scratch, double* part_host, int* bad_host, int* timeout_host,
-                             cudaEvent_t ev_begin, cudaEvent_t ev_end, cudaStream_t st) {
+                             uint64_t wait_ns, int withhold, cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                             cudaStream_t st) {
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const int64_t bps = (N + kFullP - 1) / kFullP, nblk = full_genz_blocks_per_shift(N, mixed);
     const int64_t dim = D > 1 ? D - 1 : 1;
@@ -467,7 +468,8 @@ cudaError_t launch_full_genz(const double* sites, const double* u, int64_t D, co
     e = launch_cov_chol(sites, D, cov, A, bad, st);
     if (e != cudaSuccess) return e;
     if (mixed) {
-        e = launch_full_genz_tc(A, u, D, N, S, gdev + dim, dfix, (int)dim, p, part, bad + 1, ev_begin, ev_end, st);
+        e = launch_full_genz_tc(A, u, D, N, S, gdev + dim, dfix, (int)dim, p, part, bad + 1, wait_ns, withhold,
+                                ev_begin, ev_end, st);
     } else {
         void* Ls = p;
         p += al(sizeof(double) * D * D);

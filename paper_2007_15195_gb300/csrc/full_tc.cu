@@ -31,7 +31,12 @@
 // next pair's MMAs start once panel b + 1's accumulator has been read out, so
 // they run while panel b + 1's variables are processed.  Every wait is bounded
 // by the global timer; on expiry the kernel records a timeout, waits (bounded)
-// for its copies and MMAs in flight, frees its tensor memory and returns.
+// for its copies and MMAs in flight, frees its tensor memory and returns.  The
+// limit of the point warps' waits and of the copy lane's idle time can be set
+// shorter (for tests); the drain waits keep the full 2 s, so whatever was
+// issued completes before the tensor memory is freed.  For the timeout test,
+// the copy lane can be told to issue nothing: then the first accumulator wait
+// of the point warps runs out with no copy and no MMA in flight.
 //
 // Operand layout (no swizzle, K-major): 8-row x 16-byte core matrices; within
 // a block, element (r, k) of a 16-wide chunk sits at byte
@@ -105,14 +110,14 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for the phase of the given parity; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+// Wait for the phase of the given parity; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns = kWaitNs) {
     if (mbar_try(b, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try(b, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -178,6 +183,8 @@ struct TcArgs {
     float* Y;                   // history, [tiles][nC] chunks of 32 KB
     double* part;               // per shift, per tile: sums over points 0..127 and 128..223
     int* timeout;               // set on an expired wait
+    uint64_t wait_ns;           // limit of the point warps' waits and of the copy lane's idle time
+    int withhold;               // testing: the copy lane issues no copy and no MMA
 };
 
 // Tables of the scaled factor for the tensor-core path: the blocked hi/lo
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
             int spins = 0;
             while (im < total) {
                 bool progress = false;
-                if (il < total && il < im + kTcStages) {
+                if (il < total && il < im + kTcStages && !a.withhold) {
                     const int b = 2 * lq, c = lc;
                     const bool shared = c < 4 * b, has2 = b + 1 < nP;
                     bool gate = true;
@@ -415,7 +422,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
                         const uint64_t now = global_ns();
                         if (t_idle == 0) {
                             t_idle = now;
-                        } else if (now - t_idle > kWaitNs || *(volatile int*)&abort_flag) {
+                        } else if (now - t_idle > a.wait_ns || *(volatile int*)&abort_flag) {
                             failed = true;
                             break;
                         }
@@ -445,8 +452,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) full_genz_tc_kernel(TcArgs a) {
             bool ok = true;
             // panel 2q: the shared chunks of pair q (q >= 1); panel 2q + 1: its own chunks too
             if (b > 0)
-                ok = (b & 1) ? mbar_wait(&bar_acc[1], (uint32_t)((b >> 1) & 1))
-                             : mbar_wait(&bar_acc[0], (uint32_t)(((b >> 1) - 1) & 1));
+                ok = (b & 1) ? mbar_wait(&bar_acc[1], (uint32_t)((b >> 1) & 1), a.wait_ns)
+                             : mbar_wait(&bar_acc[0], (uint32_t)(((b >> 1) - 1) & 1), a.wait_ns);
             if (points_any(!ok || *(volatile int*)&abort_flag)) {
                 if (p == 0) {
                     atomicExch(&abort_flag, 1);
@@ -518,7 +525,8 @@ size_t full_tc_scratch_bytes(int64_t D, int64_t N, int S) {
 
 cudaError_t launch_full_genz_tc(const double* A, const double* u, int64_t D, int64_t N, int S, const uint32_t* gfix,
                                 const uint32_t* dfix, int dim, void* scratch, double* part, int* timeout,
-                                cudaEvent_t ev_begin, cudaEvent_t ev_end, cudaStream_t st) {
+                                uint64_t wait_ns, int withhold, cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                                cudaStream_t st) {
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const int64_t Dp = (D + kTcB - 1) / kTcB * kTcB, nP = Dp / kTcB, nC = Dp / kTcKC;
     const int64_t tps = (N + kTcPoints - 1) / kTcPoints;
@@ -565,6 +573,8 @@ cudaError_t launch_full_genz_tc(const double* A, const double* u, int64_t D, int
     a.Y = Y;
     a.part = part;
     a.timeout = timeout;
+    a.wait_ns = (wait_ns > 0 && wait_ns < kWaitNs) ? wait_ns : kWaitNs;
+    a.withhold = withhold ? 1 : 0;
     if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
     full_genz_tc_kernel<<<(unsigned)(S * tps), kTcThreads, kTcSmem, st>>>(a);
     e = cudaGetLastError();

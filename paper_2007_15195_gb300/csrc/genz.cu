@@ -33,7 +33,9 @@
 #include <tuple>
 
 #include "cov.cuh"
+#include "f32x2.h"
 #include "special_f32.h"
+#include "special_f64.h"
 #include "vk_internal.h"
 
 namespace vk {
@@ -68,9 +70,13 @@ struct GenzSmem {
     // mean by 1/L_vv (diag), one rounding more than the definition's division.
     static constexpr int LS = (DMAX + 3) & ~3;  // row stride: 16-byte aligned rows
     __align__(16) T Lup[DMAX][LS];
+    // MIXED with four points per lane: (-Lup[t][r], -Lup[t][r]), the
+    // coefficient of both points of a pair in one 64-bit load
+    __align__(16) float2 Ln2[(MIXED && DMAX <= 21) ? DMAX : 1][LS];
     __align__(16) T Lz[DMAX];
     __align__(16) T up[DMAX];  // MIXED: u_v / L_vv;  FP64: u_v
     uint32_t gl[DMAX];         // FP64: g_t;  MIXED: round(g_t 2^32 / N)
+    uint64_t g64[MIXED ? 1 : DMAX];  // FP64: round(g_t 2^64 / N)
     double part_num[kMaxUnits], part_den[kMaxUnits];
     double e0, ec0;
     float le2_0;  // log2 e0 when e0 < 2^-64 (mixed path)
@@ -79,17 +85,28 @@ struct GenzSmem {
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// Bytes of shared memory for a CTA of `warps` warps on problems with <= max_S shifts.
+// FP64 path, per warp and step of its current shift: the lattice coordinate's
+// multiplier and shift in 64-bit fixed point (round(g_t 2^64 / N), Delta_t 2^64)
+// and the step's coefficient -L_{t+1,t} and 1/L_{t+1,t+1}.
+struct Step64 {
+    uint64_t G, D;
+    double nlz, rdiag;
+};
+
+// Bytes of shared memory for a CTA of `warps` warps on problems with <= max_S
+// shifts: the fixed part, then (mixed) the shifts in fixed point and the
+// per-warp step constants, or (FP64) the tail tables and the per-warp steps.
 template <int DMAX, bool MIXED>
 constexpr size_t smem_bytes(int max_S, int warps) {
     return align16(sizeof(GenzSmem<DMAX, MIXED>)) +
-           (MIXED ? align16((size_t)max_S * DMAX * 4) + (size_t)warps * DMAX * 16 : 0);
+           (MIXED ? align16((size_t)max_S * DMAX * 4) + (size_t)warps * DMAX * 16
+                  : align16(sizeof(special64::Tables64)) + (size_t)warps * DMAX * sizeof(Step64));
 }
 
 extern __shared__ __align__(16) unsigned char vk_smem[];
 
 // The dynamic tail: dfix row of shift s, and the step constants of a warp:
-// {L_{t+1,t}/L_{t+1,t+1}, round(g_t 2^32/N), shift_t 2^32, 0}, one 16-byte load per step.
+// {-L_{t+1,t}/L_{t+1,t+1}, round(g_t 2^32/N), shift_t 2^32, 0}, one 16-byte load per step.
 template <int DMAX>
 __device__ __forceinline__ uint32_t* dfix_row(int s) {
     return (uint32_t*)(vk_smem + align16(sizeof(GenzSmem<DMAX, true>))) + s * DMAX;
@@ -97,6 +114,16 @@ __device__ __forceinline__ uint32_t* dfix_row(int s) {
 template <int DMAX>
 __device__ __forceinline__ float4* stepw_of(int max_S, int warp) {
     return (float4*)(vk_smem + align16(sizeof(GenzSmem<DMAX, true>)) + align16((size_t)max_S * DMAX * 4)) +
+           warp * DMAX;
+}
+template <int DMAX>
+__device__ __forceinline__ special64::Tables64& tables64() {
+    return *reinterpret_cast<special64::Tables64*>(vk_smem + align16(sizeof(GenzSmem<DMAX, false>)));
+}
+template <int DMAX>
+__device__ __forceinline__ Step64* step64_of(int warp) {
+    return reinterpret_cast<Step64*>(vk_smem + align16(sizeof(GenzSmem<DMAX, false>)) +
+                                     align16(sizeof(special64::Tables64))) +
            warp * DMAX;
 }
 
@@ -107,12 +134,6 @@ __device__ __forceinline__ void phi_pair64(double z, double& e, double& ec) {
     ec = (z < 0.0) ? 1.0 - t : t;
 }
 
-// Phi^{-1}(p) given p and q = 1 - p: from the smaller tail, clamped at 2^-1000.
-__device__ __forceinline__ double phiinv_pq64(double p, double q) {
-    const double lo = 9.3326361850321887899e-302;  // 2^-1000
-    const double pc = fmax(p, lo), qc = fmax(q, lo);
-    return (pc <= qc) ? normcdfinv(pc) : -normcdfinv(qc);
-}
 
 // 2^-E as a double (0 once below the normal range).
 __device__ __forceinline__ double pow2_neg(int E) {
@@ -274,14 +295,14 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
                                           float (&g)[P], const uint32_t (&kk)[P]) {
     const float* lup = sm.Lup[t];
     const float4 c = sc[t];
-    const float lz = c.x;
+    const float nlz = c.x;  // -L_{t+1,t}/L_{t+1,t+1}
     const uint32_t G = __float_as_uint(c.y), Dt = __float_as_uint(c.z);
     if constexpr (P == 1) {  // one point per lane: the per-point form keeps fewer values live
         if (!FIRST) g[0] = __fmul_rn(g[0], e[0]);
         const uint32_t X = kk[0] * G + Dt;
         const float w = __fmul_rn(fabsf(__int2float_rn((int32_t)X)), 0x1p-31f);  // |int32(X)| 2^-31
         const float yv = special::phiinv_pq(__fmul_rn(w, e[0]), fmaf(w, ec[0], __fsub_rn(1.0f, w)));
-        const float z = fmaf(-lz, yv, R[0][0]);
+        const float z = fmaf(nlz, yv, R[0][0]);
 #pragma unroll
         for (int r = 0; r < W; ++r) R[0][r] = fmaf(-lup[r], yv, R[0][r + 1]);
         special::phi_pair_fast(z, e[0], ec[0]);
@@ -311,17 +332,61 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const float yv = special::phiinv_finish(pp[p], qq[p], y[p]);
-        const float z = fmaf(-lz, yv, R[p][0]);
+        const float z = fmaf(nlz, yv, R[p][0]);
 #pragma unroll
         for (int r = 0; r < W; ++r) R[p][r] = fmaf(-lup[r], yv, R[p][r + 1]);
         special::phi_pair_fast(z, e[p], ec[p]);
     }
 }
 
+// Four points per lane as two f32x2 pairs (points k, k + 32 | k + 64, k + 96):
+// each pair's whole step -- the lattice-weighted probabilities, both
+// polynomials, the products and the conditional-mean updates -- in packed
+// instructions, element by element the arithmetic of fast_step (bit-identical
+// values).  The two pairs are independent dependency chains; the lattice
+// coordinates, special-function-unit calls and selects stay per point, and
+// one full-warp vote per step decides the tail pieces for all four points.
+template <int DMAX, int W, bool FIRST>
+__device__ __forceinline__ void fast_step4(const GenzSmem<DMAX, true>& sm, const float4* sc, int t,
+                                           x2::f2 (&R)[2][DMAX - 1], x2::f2 (&e)[2], x2::f2 (&ec)[2],
+                                           x2::f2 (&g)[2], const uint32_t (&kk)[4]) {
+    const x2::f2* ln = reinterpret_cast<const x2::f2*>(sm.Ln2[t]);
+    const float4 c = sc[t];
+    const x2::f2 nlz = x2::splat(c.x);
+    const uint32_t G = __float_as_uint(c.y), Dt = __float_as_uint(c.z);
+    x2::f2 pp[2], qq[2], f[2];
+    bool tl[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!FIRST) g[h] = x2::mul(g[h], e[h]);  // g = e_1 ... e_t
+        const uint32_t X0 = kk[2 * h] * G + Dt, X1 = kk[2 * h + 1] * G + Dt;
+        const x2::f2 w = x2::pack(__fmul_rn(fabsf(__int2float_rn((int32_t)X0)), 0x1p-31f),
+                                  __fmul_rn(fabsf(__int2float_rn((int32_t)X1)), 0x1p-31f));
+        pp[h] = x2::mul(w, e[h]);
+        qq[h] = x2::fma(w, ec[h], x2::sub(x2::splat(1.0f), w));
+        f[h] = special::phiinv_central2(pp[h], qq[h], tl[2 * h], tl[2 * h + 1]);
+    }
+    if (__any_sync(0xffffffffu, tl[0] || tl[1] || tl[2] || tl[3])) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) f[h] = special::phiinv_tail2(pp[h], qq[h], tl[2 * h], tl[2 * h + 1], f[h]);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const x2::f2 y = x2::mul(x2::sub(pp[h], qq[h]), f[h]);
+        const x2::f2 z = x2::fma(nlz, y, R[h][0]);
+#pragma unroll
+        for (int r = 0; r < W; ++r) R[h][r] = x2::fma(ln[r], y, R[h][r + 1]);
+        special::phi_pair_fast2(z, e[h], ec[h]);
+    }
+}
+
 // Width step between phases: 4 up to 21 variables; 6 above, where fewer
 // copies of the step body (instruction cache) beat the extra padding FMAs
 // (measured: m = 30 5.7 % faster, m <= 16 0.7 % slower with 6).
-__host__ __device__ constexpr int phase_step(int dmax) { return dmax <= 21 ? 4 : 6; }
+#ifndef VK_PHASE_STEP_SMALL
+#define VK_PHASE_STEP_SMALL 4
+#endif
+__host__ __device__ constexpr int phase_step(int dmax) { return dmax <= 21 ? VK_PHASE_STEP_SMALL : 6; }
 
 // Steps t <= t' < q (t >= 1) of a term with q steps, in phases of update width
 // W, W - step, ...: a step needs width q - t' - 1, so the phase of width W ends
@@ -346,6 +411,22 @@ __device__ __forceinline__ void fast_phases(const GenzSmem<DMAX, true>& sm, cons
     if constexpr (WN > 0) fast_phases<DMAX, P, WN, CAPTURE>(sm, sc, t_end, q, cut, R, e, ec, g, gd, kk);
 }
 
+template <int DMAX, int W, bool CAPTURE>
+__device__ __forceinline__ void fast_phases4(const GenzSmem<DMAX, true>& sm, const float4* sc, int t, int q,
+                                             int cut, x2::f2 (&R)[2][DMAX - 1], x2::f2 (&e)[2], x2::f2 (&ec)[2],
+                                             x2::f2 (&g)[2], x2::f2 (&gd)[2], const uint32_t (&kk)[4]) {
+    constexpr int WN = W - phase_step(DMAX);
+    const int t_end = (WN > 0) ? max(t, min(q, q - 1 - WN)) : q;
+    for (int tt = t; tt < t_end; ++tt) {
+        if (CAPTURE && tt == cut) {
+            gd[0] = g[0];
+            gd[1] = g[1];
+        }
+        fast_step4<DMAX, W, false>(sm, sc, tt, R, e, ec, g, kk);
+    }
+    if constexpr (WN > 0) fast_phases4<DMAX, WN, CAPTURE>(sm, sc, t_end, q, cut, R, e, ec, g, gd, kk);
+}
+
 template <int DMAX, int P, bool CAPTURE>
 __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm, int q, int c, int s,
                                                  int max_S, int64_t k_begin, int64_t k_end,
@@ -356,10 +437,49 @@ __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm,
     const uint32_t* dfs = dfix_row<DMAX>(s);
     __syncwarp();
     for (int t = lane; t < q; t += 32)
-        sc[t] = make_float4(sm.Lz[t], __uint_as_float(sm.gl[t]), __uint_as_float(dfs[t]), 0.0f);
+        sc[t] = make_float4(-sm.Lz[t], __uint_as_float(sm.gl[t]), __uint_as_float(dfs[t]), 0.0f);
     __syncwarp();
     const float e0f = (float)sm.e0, ec0f = (float)sm.ec0;
     Kahan32 kn, kd;
+    if constexpr (P == 4) {
+        for (int64_t kb = k_begin; kb < k_end; kb += 128) {
+            x2::f2 R[2][DMAX - 1];
+            uint32_t kk[4];
+            bool valid[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int64_t k = kb + p * 32 + lane;
+                valid[p] = k < k_end;
+                kk[p] = (uint32_t)(valid[p] ? k : k_begin);
+            }
+#pragma unroll
+            for (int r = 0; r < DMAX - 1; ++r) R[0][r] = R[1][r] = x2::splat(sm.up[1 + r]);
+            x2::f2 e[2], ec[2], g[2], gd[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                e[h] = x2::splat(e0f);
+                ec[h] = x2::splat(ec0f);
+                g[h] = gd[h] = x2::splat(1.0f);  // c = 1: e_0 alone (factored out)
+            }
+            fast_step4<DMAX, W0, true>(sm, sc, 0, R, e, ec, g, kk);  // q >= 1: step 0 at full width
+            fast_phases4<DMAX, W0, CAPTURE>(sm, sc, 1, q, c, R, e, ec, g, gd, kk);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float g0, g1, e0, e1, d0, d1;
+                x2::unpack(g[h], g0, g1);
+                x2::unpack(e[h], e0, e1);
+                x2::unpack(gd[h], d0, d1);
+                if (valid[2 * h]) {
+                    kd.add(CAPTURE ? d0 : g0);
+                    kn.add(__fmul_rn(g0, e0));
+                }
+                if (valid[2 * h + 1]) {
+                    kd.add(CAPTURE ? d1 : g1);
+                    kn.add(__fmul_rn(g1, e1));
+                }
+            }
+        }
+    } else {
     for (int64_t kb = k_begin; kb < k_end; kb += 32 * P) {
         float R[P][DMAX - 1], e[P], ec[P], g[P], gd[P];
         uint32_t kk[P];
@@ -386,43 +506,90 @@ __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm,
             }
         }
     }
+    }
     acc_num += kn.value();
     acc_den += kd.value();
 }
 
 // ------------------------------- FP64 path ---------------------------------
 
+// Lattice coordinate in 64-bit fixed point to a double: V 2^-63 for
+// 0 <= V <= 2^63, rounded to 53 bits (integer instructions only).
+__device__ __forceinline__ double fix63_to_f64(uint64_t V) {
+    if (V == 0) return 0.0;
+    const int lz = __clzll((long long)V);
+    const uint64_t m = V << lz;  // bit 63 set
+    const uint64_t bits = ((uint64_t)(1023 - lz) << 52) + ((m >> 11) & 0xFFFFFFFFFFFFFull) + ((m >> 10) & 1);
+    return __longlong_as_double((long long)bits);
+}
+
+// One FP64 step t (lattice coordinate t, variable t + 1 next) of a point:
+// update width W.  x = frac(k g_t / N + Delta_t) in 64-bit fixed point
+// X = k G_t + D_t mod 2^64; the tent w = 1 - |2x - 1| = |int64(X)| 2^-63
+// and |2x - 1| = 1 - w from the same integer.
+template <int DMAX, int W>
+__device__ __forceinline__ void fp64_step(const GenzSmem<DMAX, false>& sm, const special64::Tables64& tb,
+                                          const Step64& st, int t, uint32_t k, double (&R)[DMAX - 1], double& e,
+                                          double& ec) {
+    const uint64_t X = (uint64_t)k * st.G + st.D;
+    const uint64_t V = ((int64_t)X < 0) ? (0ull - X) : X;  // |int64(X)| <= 2^63
+    const double w = fix63_to_f64(V);
+    const double a = fix63_to_f64((1ull << 63) - V);
+    const double pp = w * e;
+    const double qq = fma(w, ec, a);
+    const double y = special64::phiinv_pq(tb, pp, qq);
+    const double* lup = sm.Lup[t];
+    const double acc = fma(st.nlz, y, R[0]);
+#pragma unroll
+    for (int r = 0; r < W; ++r) R[r] = fma(-lup[r], y, R[r + 1]);
+    special64::phi_pair(tb, acc * st.rdiag, e, ec);
+}
+
+// Steps t <= t' < q in phases of update width W, W - step, ... (as the mixed path).
+template <int DMAX, int W>
+__device__ __forceinline__ void fp64_phases(const GenzSmem<DMAX, false>& sm, const special64::Tables64& tb,
+                                            const Step64* st, int t, int q, int c, uint32_t k,
+                                            double (&R)[DMAX - 1], double& e, double& ec, double& f, double& fc) {
+    constexpr int WN = W - phase_step(DMAX);
+    const int t_end = (WN > 0) ? max(t, min(q, q - 1 - WN)) : q;
+    for (int tt = t; tt < t_end; ++tt) {
+        f *= e;                   // e_0 ... e_tt
+        if (tt + 1 == c) fc = f;  // the c-dim CDF sample of the leading block
+        fp64_step<DMAX, W>(sm, tb, st[tt], tt, k, R, e, ec);
+    }
+    if constexpr (WN > 0) fp64_phases<DMAX, WN>(sm, tb, st, t_end, q, c, k, R, e, ec, f, fc);
+}
+
+// 2^64 g / N rounded to the nearest integer (g < N < 2^32), by two steps of
+// long division.
+__device__ __forceinline__ uint64_t fix64_ratio(uint32_t g, uint64_t N) {
+    const uint64_t a = ((uint64_t)g << 32), q1 = a / N, r1 = a % N;
+    const uint64_t b = r1 << 32, q2 = b / N, r2 = b % N;
+    return (q1 << 32) + q2 + ((2 * r2 >= N) ? 1u : 0u);
+}
+
 template <int DMAX>
 __device__ __forceinline__ void genz_points_fp64(const GenzSmem<DMAX, false>& sm, const ProbDev& P,
                                                  int q, int c, int s, int64_t k_begin, int64_t k_end,
                                                  double& acc_num, double& acc_den) {
-    constexpr int W = DMAX - 2;
+    constexpr int W0 = (DMAX - 2 > 0) ? DMAX - 2 : 1;
     const int lane = threadIdx.x & 31;
+    const special64::Tables64& tb = tables64<DMAX>();
+    Step64* st = step64_of<DMAX>(threadIdx.x >> 5);
     const double* dl = P.delta + (int64_t)s * P.dim;
-    const uint64_t N = (uint64_t)P.N;
-    const double Nd = (double)P.N, invN = 1.0 / Nd;
+    __syncwarp();
+    for (int t = lane; t < q; t += 32) {
+        // Delta = M 2^-53 exactly (53-bit shifts): D = M 2^11
+        const uint64_t M = (uint64_t)__double2ull_rn(dl[t] * 9007199254740992.0);
+        st[t] = Step64{sm.g64[t], M << 11, -sm.Lz[t], sm.diag[t + 1]};
+    }
+    __syncwarp();
     for (int64_t k = k_begin + lane; k < k_end; k += 32) {
         double R[DMAX - 1];
 #pragma unroll
         for (int r = 0; r < DMAX - 1; ++r) R[r] = sm.up[1 + r];
         double e = sm.e0, ec = sm.ec0, f = 1.0, fc = 1.0;
-        for (int t = 0; t < q; ++t) {
-            f *= e;  // e_0 ... e_t
-            if (t + 1 == c) fc = f;  // the c-dim CDF sample of the leading block
-            const uint64_t rr = ((uint64_t)k * (uint64_t)sm.gl[t]) % N;
-            double x = __dadd_rn((double)rr * invN, dl[t]);
-            if (x >= 1.0) x -= 1.0;
-            const double a = fabs(__dsub_rn(__dmul_rn(2.0, x), 1.0));
-            const double w = __dsub_rn(1.0, a);
-            const double pp = __dmul_rn(w, e);
-            const double qq = __dadd_rn(a, __dmul_rn(w, ec));
-            const double y = phiinv_pq64(pp, qq);
-            const double* lup = sm.Lup[t];
-            const double acc = fma(-sm.Lz[t], y, R[0]);
-#pragma unroll
-            for (int r = 0; r < W; ++r) R[r] = fma(-lup[r], y, R[r + 1]);
-            phi_pair64(acc * sm.diag[t + 1], e, ec);
-        }
+        fp64_phases<DMAX, W0>(sm, tb, st, 0, q, c, (uint32_t)k, R, e, ec, f, fc);
         acc_den += fc;
         acc_num += f * e;
     }
@@ -489,10 +656,14 @@ constexpr int kModeFP64 = 0, kModeFast = 1, kModeSafe = 2;
 #ifndef VK_CAP_P2_LARGE
 #define VK_CAP_P2_LARGE 128
 #endif
+#ifndef VK_CAP_P4
+#define VK_CAP_P4 168
+#endif
 __host__ __device__ constexpr int reg_cap(int dmax, int p, int mode) {
     return dmax > 32            ? (mode == kModeFast ? 128 : 255)
            : mode != kModeFast ? 128
            : p == 1            ? (dmax <= 16 ? VK_CAP_P1_SMALL : VK_CAP_P1_LARGE)
+           : p == 4            ? VK_CAP_P4
                                : (dmax <= 16 ? VK_CAP_P2_SMALL : VK_CAP_P2_LARGE);
 }
 __host__ __device__ constexpr int max_threads(int dmax, int p, int mode) {
@@ -555,6 +726,10 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
     const int warp = threadIdx.x >> 5;
     const int n_warps = blockDim.x >> 5;
 
+    if constexpr (!MIXED) {
+        special64::load_tables(tables64<DMAX>());
+        __syncthreads();
+    }
     const int n_run = src.dev_count ? min(*src.dev_count, src.n_items) : src.n_items;
     for (int it = blockIdx.x; it < n_run; it += gridDim.x) {
         int2 item;
@@ -664,6 +839,7 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
                         val = sm.A[v][t];
                 }
                 sm.Lup[t][r] = val;
+                if constexpr (MIXED && DMAX <= 21) sm.Ln2[t][r] = make_float2(-(float)val, -(float)val);
             }
             for (int v = threadIdx.x; v < DMAX; v += blockDim.x) {
                 T val = (T)0, lz = (T)0;
@@ -682,6 +858,8 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
                 sm.up[v] = val;
                 sm.Lz[v] = lz;
                 if (v < q) sm.gl[v] = MIXED ? Pd.gfix[v] : Pd.g[v];
+                if constexpr (!MIXED)
+                    if (v < q) sm.g64[v] = fix64_ratio(Pd.g[v], (uint64_t)Pd.N);
             }
             if constexpr (MIXED) {
                 for (int x = threadIdx.x; x < S * DMAX; x += blockDim.x) {
@@ -904,7 +1082,36 @@ __global__ void eval_special_kernel(int which, const float* __restrict__ x, int6
     out[i] = r;
 }
 
+// FP64 forms of the FP64 path: which = 0: Phi(x); 1: 1 - Phi(x); 2: Phi^{-1}(x)
+// given p = x and q = 1 - x; 3: Phi^{-1}(1 - x) given q = x and p = 1 - x, i.e.
+// -Phi^{-1}(x) taken from the upper argument.
+__global__ void eval_special64_kernel(int which, const double* __restrict__ x, int64_t n,
+                                      double* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char tb_smem[];
+    special64::Tables64& tb = *reinterpret_cast<special64::Tables64*>(tb_smem);
+    special64::load_tables(tb);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    double e, ec, r;
+    switch (which) {
+        case 0: special64::phi_pair(tb, v, e, ec); r = e; break;
+        case 1: special64::phi_pair(tb, v, e, ec); r = ec; break;
+        case 2: r = special64::phiinv_pq(tb, v, 1.0 - v); break;
+        case 3: r = special64::phiinv_pq(tb, 1.0 - v, v); break;
+        default: r = NAN;
+    }
+    out[i] = r;
+}
+
 }  // namespace
+
+cudaError_t launch_eval_special64(int which, const double* x, int64_t n, double* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    eval_special64_kernel<<<(int)((n + 255) / 256), 256, sizeof(special64::Tables64), st>>>(which, x, n, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_eval_special(int which, const float* x, int64_t n, float* out, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
@@ -977,16 +1184,24 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
         if (t.points >= 2)                                                                       \
             return launch_one<DM, 2, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);    \
         return launch_one<DM, 1, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);
+#define VK_CASE4(IDX, DM)                                                                        \
+    case IDX:                                                                                    \
+        if (!mixed) return launch_one<DM, 1, kModeFP64>(VK_ARGS, nullptr, nullptr, st);           \
+        if (t.points >= 4)                                                                       \
+            return launch_one<DM, 4, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);    \
+        if (t.points >= 2)                                                                       \
+            return launch_one<DM, 2, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);    \
+        return launch_one<DM, 1, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);
 #define VK_CASE1(IDX, DM)                                                                        \
     case IDX:                                                                                    \
         if (!mixed) return launch_one<DM, 1, kModeFP64>(VK_ARGS, nullptr, nullptr, st);           \
         return launch_one<DM, 1, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);
     static_assert(kNumBuckets == 9, "bucket table");
     switch (bucket) {
-        VK_CASE(0, 9)
-        VK_CASE(1, 13)
-        VK_CASE(2, 17)
-        VK_CASE(3, 21)
+        VK_CASE4(0, 9)
+        VK_CASE4(1, 13)
+        VK_CASE4(2, 17)
+        VK_CASE4(3, 21)
         VK_CASE(4, 25)
         VK_CASE(5, 29)
         VK_CASE(6, 32)
@@ -996,6 +1211,7 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
             return cudaErrorInvalidValue;
     }
 #undef VK_CASE
+#undef VK_CASE4
 #undef VK_CASE1
 #undef VK_ARGS
 }

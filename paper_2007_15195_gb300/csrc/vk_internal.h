@@ -157,13 +157,17 @@ int64_t full_genz_blocks_per_shift(int64_t N, bool mixed);
 cudaError_t launch_full_genz(const double* sites, const double* u, int64_t D, const vecchia_cov& cov, int64_t N,
                              int S, bool mixed, const uint32_t* g_host, const uint32_t* gfix_host,
                              uint64_t seed, void* scratch, double* part_host, int* bad_host, int* timeout_host,
-                             cudaEvent_t ev_begin, cudaEvent_t ev_end, cudaStream_t st);
+                             uint64_t wait_ns, int withhold, cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                             cudaStream_t st);
 // The mixed recursion on the tensor cores (full_tc.cu), given the FP64 factor A.
+// wait_ns: limit of its progress waits (0: the built-in 2 s); withhold: the
+// copy lane issues nothing (tests of the timeout path only).
 size_t full_tc_scratch_bytes(int64_t D, int64_t N, int S);
 int64_t full_tc_blocks_per_shift(int64_t N);
 cudaError_t launch_full_genz_tc(const double* A, const double* u, int64_t D, int64_t N, int S, const uint32_t* gfix,
                                 const uint32_t* dfix, int dim, void* scratch, double* part, int* timeout,
-                                cudaEvent_t ev_begin, cudaEvent_t ev_end, cudaStream_t st);
+                                uint64_t wait_ns, int withhold, cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                                cudaStream_t st);
 
 // sites_out[k] = sites[perm[k]], u_out[k] = u[perm[k]]; *bad = 1 on an index out of range.
 cudaError_t launch_gather(const int32_t* perm, const double* sites, const double* u, int64_t D,
@@ -171,6 +175,7 @@ cudaError_t launch_gather(const int32_t* perm, const double* sites, const double
 
 // The FP32 special functions of the mixed path on n device values (diagnostic).
 cudaError_t launch_eval_special(int which, const float* x, int64_t n, float* out, cudaStream_t st);
+cudaError_t launch_eval_special64(int which, const double* x, int64_t n, double* out, cudaStream_t st);
 
 int device_sm_count(int device);
 

@@ -2,8 +2,10 @@
 square, exact maxmin order, Matern nu in {0.5, 1.5} with range 0.05,
 u ~ U[0, 2], m = 30, N = 8,192 x S = 16.  The full mixed-precision
 evaluation is checked term by term on sampled sites against the oracle's
-one-site evaluation; the FP64 path on an ordered prefix (itself a valid
-problem: every neighbour of site i < K is among the first K sites)."""
+one-site evaluation; the FP64 path at full size, its per-shift partial means
+on sampled terms against the oracle's (1e-10) and its log P against the mixed
+one (the mixed tolerance), and on an ordered prefix (itself a valid problem:
+every neighbour of site i < K is among the first K sites)."""
 import numpy as np
 import pytest
 
@@ -68,3 +70,22 @@ def test_large_fp64_on_ordered_prefix(ctx, large_ordered):
     assert np.allclose(den[idx], oden, rtol=1e-10, atol=0)
     mlp, mse = B.vecchia_log_cdf(ctx, sp, nbr, prob.m, prob.cov, up, prob.N, prob.S, 3, B.MIXED)
     assert abs(mlp - lp) <= mixed_tol(lp)
+
+
+def test_large_fp64_full_size(ctx, large_ordered):
+    import torch
+    prob, s, u = large_ordered
+    ds, du = torch.from_numpy(s).cuda(), torch.from_numpy(u).cuda()
+    nbr = B.vecchia_neighbors(ctx, ds, prob.m)
+    lp, se, terms, num, den = B.vecchia_log_cdf_terms(ctx, ds, nbr, prob.m, prob.cov, du, prob.N, prob.S, 0,
+                                                      B.FP64)
+    assert np.isfinite(lp) and lp < 0
+    rng = np.random.default_rng(11)
+    idx = np.unique(np.concatenate([[0, 1, 2, 29, 30, 31, 32, prob.D - 1], rng.integers(33, prob.D, 32)]))
+    nb_h = nbr.cpu().numpy()
+    onum, oden = O.vecchia_partials(s, nb_h, prob.m, prob.cov, u, prob.N, prob.S, 0, idx=idx)
+    num, den = num.cpu().numpy(), den.cpu().numpy()
+    assert np.allclose(num[idx], onum, rtol=1e-10, atol=0), np.max(np.abs(num[idx] / onum - 1))
+    assert np.allclose(den[idx], oden, rtol=1e-10, atol=0), np.max(np.abs(den[idx] / oden - 1))
+    mlp, _ = B.vecchia_log_cdf(ctx, ds, nbr, prob.m, prob.cov, du, prob.N, prob.S, 0, B.MIXED)
+    assert abs(mlp - lp) <= mixed_tol(lp), (mlp, lp)

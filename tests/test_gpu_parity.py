@@ -301,7 +301,8 @@ def test_tiles_change_only_sum_order(ctx):
     for prec in (B.FP64, B.MIXED):
         B.vecchia_reset_tiles(ctx)
         ref = B.vecchia_log_cdf(ctx, s, nbr, 20, prob.cov, u, prob.N, prob.S, 1, prec)
-        for warps, points, slices, groups in [(1, 1, 1, 1), (8, 2, 1, 8), (4, 2, 4, 2), (16, 1, 2, 3)]:
+        for warps, points, slices, groups in [(1, 1, 1, 1), (8, 2, 1, 8), (4, 2, 4, 2), (16, 1, 2, 3), (4, 4, 1, 1),
+                                              (2, 4, 1, 3), (4, 4, 2, 2)]:
             B.vecchia_set_tile(ctx, prec, -1, warps, points, slices, groups)
             lp, se = B.vecchia_log_cdf(ctx, s, nbr, 20, prob.cov, u, prob.N, prob.S, 1, prec)
             if slices == 1:  # same points per lane in the same order: bit-identical
@@ -311,14 +312,37 @@ def test_tiles_change_only_sum_order(ctx):
         B.vecchia_reset_tiles(ctx)
 
 
-def test_mixed_underflow_falls_back_to_fp64(ctx):
-    """Thresholds far below the mean: FP32 conditional probabilities underflow,
-    the flagged terms are re-evaluated in FP64 and the result equals FP64's."""
+@pytest.mark.parametrize("m,N", [(3, 1000), (8, 77), (12, 4096), (16, 129), (20, 1000)])
+def test_four_points_per_lane_equal_one(ctx, m, N):
+    """Four points per lane (two f32x2 pairs, blocks of up to 21 variables)
+    compute element by element the arithmetic of one point per lane: the
+    per-shift partial means must agree bit for bit, with ragged point counts."""
+    prob = inputs.small_random(300, 14 + m, m=m, N=N, S=4)
+    _, s, u, nbr = oracle_prepare(prob)
+    out = {}
+    for pts in (1, 4):
+        B.vecchia_set_tile(ctx, B.MIXED, -1, 4, pts, 1, 1)
+        out[pts] = B.vecchia_log_cdf_terms(ctx, s, nbr, m, prob.cov, u, prob.N, prob.S, 2, B.MIXED)
+    B.vecchia_reset_tiles(ctx)
+    assert out[1][0] == out[4][0] and out[1][1] == out[4][1]
+    assert np.array_equal(np.asarray(out[1][3]), np.asarray(out[4][3]))
+    assert np.array_equal(np.asarray(out[1][4]), np.asarray(out[4][4]))
+
+
+def test_mixed_underflow_falls_back_to_log_space(ctx):
+    """Thresholds far below the mean: FP32 conditional probabilities underflow
+    in the fast mixed form, whose lattice means then fall below 2^-40; those
+    terms are flagged and re-evaluated by the log-space FP32 form (probabilities
+    carried as log2 below 2^-64), so the mixed result stays within the mixed
+    tolerance of the oracle (and of the FP64 path)."""
     prob = inputs.small_random(60, 13, m=6, u_mean=-14.0, u_sd=0.5, N=256, S=4)
     _, s, u, nbr = oracle_prepare(prob)
+    ref, _ = O.log_cdf(s, nbr, 6, prob.cov, u, prob.N, prob.S, 0)
     lp64, se64 = B.vecchia_log_cdf(ctx, s, nbr, 6, prob.cov, u, prob.N, prob.S, 0, B.FP64)
     lpm, sem = B.vecchia_log_cdf(ctx, s, nbr, 6, prob.cov, u, prob.N, prob.S, 0, B.MIXED)
-    assert math.isfinite(lpm)
+    assert math.isfinite(lpm) and ref < -100.0  # deep in the tail
+    assert abs(lp64 - ref) <= 1e-10 * abs(ref)
+    assert abs(lpm - ref) <= mixed_tol(ref)
     assert abs(lpm - lp64) <= mixed_tol(lp64)
 
 

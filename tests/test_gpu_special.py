@@ -65,3 +65,56 @@ def test_quantile_from_log2(ctx):
     y, lf = _run(ctx, 4, lr2)
     ref = special.ndtri(np.exp2(lf))
     assert np.max(np.abs(y - ref) / np.abs(ref)) < 1e-6
+
+
+# ---- FP64 forms of the FP64 path (vecchia_eval_special64) ----
+
+def _run64(ctx, which, x):
+    import torch
+    xs = torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+    return B.vecchia_eval_special64(ctx, which, xs).cpu().numpy()
+
+
+def test_phi64_relative_error_of_the_smaller_tail(ctx):
+    # Phi(-a) = exp(-a^2/2) R(a): R piecewise (fit ~5e-16), the exponential
+    # table-driven with a^2/2 carried exactly; a few 1e-16 overall.  The
+    # reference is scipy's ndtr, which rounds the square of x/sqrt(2) before
+    # exponentiating it: its own relative error grows like 2^-53 a^2 in the
+    # tail, which the bound allows for.
+    x = np.concatenate([np.linspace(-37.5, 37.5, 400001), [0.0, -1e-300, 1e-300, -0.125, 0.125]])
+    e = _run64(ctx, 0, x)
+    ec = _run64(ctx, 1, x)
+    small = np.where(x < 0, e, ec)
+    small_ref = special.ndtr(-np.abs(x))
+    rel = np.abs(small - small_ref) / small_ref
+    bound = 2e-15 + 4.5e-16 * x * x
+    assert np.all(rel < bound), (np.max(rel / bound), x[np.argmax(rel / bound)])
+    core = np.abs(x) <= 2.0
+    assert np.max(rel[core]) < 4e-15
+    assert np.max(np.abs(e - special.ndtr(x))) < 4.5e-16  # two units in the last place below 1
+    assert np.all(e + ec == pytest.approx(1.0, abs=2e-16))
+
+
+def test_phi64_below_the_normal_range(ctx):
+    x = np.linspace(-38.4, -37.6, 801)  # Phi(x) between ~1e-323 and 2^-1022
+    e = _run64(ctx, 0, x)
+    ref = special.ndtr(x)
+    assert np.all(np.abs(e - ref) <= 1e-3 * ref + 5e-324)
+
+
+def test_quantile64_from_either_tail(ctx):
+    # one Halley step from the FP32 first guess: ~1e-15 relative
+    p = np.concatenate([10.0 ** -np.linspace(300.0, 0.31, 40001), np.linspace(0.49, 0.5, 1001)])
+    y = _run64(ctx, 2, p)
+    ref = special.ndtri(p)
+    err = np.abs(y - ref) / np.maximum(np.abs(ref), 1e-300)
+    assert np.max(err[p < 0.4]) < 2e-14, (np.max(err), p[np.argmax(err)])
+    assert np.max(np.abs(y - ref)[p >= 0.4]) < 1e-15
+    yu = _run64(ctx, 3, p)  # Phi^{-1}(1 - p) from q = p
+    assert np.max(np.abs(yu + ref) / np.maximum(np.abs(ref), 1e-300)) < 2e-14
+
+
+def test_quantile64_clamps_at_2_pow_minus_1000(ctx):
+    y = _run64(ctx, 2, np.array([0.0, 1e-310, 2.0 ** -1000, 2.0 ** -999]))
+    ref = special.ndtri(np.array([2.0 ** -1000, 2.0 ** -1000, 2.0 ** -1000, 2.0 ** -999]))
+    assert np.max(np.abs(y - ref) / np.abs(ref)) < 2e-14
