@@ -15,8 +15,13 @@ buffers, the Genz kernel's fraction of the FP32-pipe peak, and the oracle
 itself on a bounded sample of the workload on the host cores.
 
 `--impl reference` times the oracle (the CPU restatement of the method) on the
-same metric: each step evaluates a bounded sample of terms and is scaled to a
-full evaluation.
+same metric: the K timed steps split one full evaluation (seed 0, all 2,500
+terms) into K contiguous slices of terms, so their summed time is one complete
+oracle evaluation, timed and not extrapolated.
+
+The default run also appends compact measurements of the batched (4,096
+problems), serving (Poisson arrivals) and large (D = 100,000) workloads, and a
+latency distribution of both precisions over distinct seeds.
 """
 import argparse
 import json
@@ -59,9 +64,14 @@ def workload_for(m):
 #          row t + 1, i.e. q(q+1)/2 FMAs per point of a q-neighbour term.
 #          Selects, min/max, integer and special-function-unit instructions
 #          are not counted.
-SM_COUNT = 152
+SM_COUNT = 152          # replaced by the device's SM count (init_peaks)
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ = 2070.0     # replaced by the measured maximum SM clock (init_peaks)
+PEAK_SOURCE = "GB300 nominal: 152 SMs, 2070 MHz"
+# FP64 lanes per SM (an FMA counting once): GB300's FP64 rate is 1/64 of its
+# FP32 rate (1.25 TFLOP/s FP64 nominal = 152 SMs x 2 FMA lanes x 2 flops x
+# 2.07 GHz).
+FP64_LANES_PER_SM = 2
 ALG_OPS_STEP = 34
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the Genz kernel on the headline workload (m = 20, built-in tile:
@@ -72,6 +82,44 @@ GENZ_TRAFFIC_BYTES_M20 = 363_264
 # one ncu capture of that launch: 13.26 GB read + 1.56 GB written.
 FULL_TC_TRAFFIC_BYTES_D2500 = 14_817_437_000
 FULL_TC_POINTS, FULL_TC_PANEL, FULL_TC_CHUNK = 224, 64, 16
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def init_peaks(device):
+    """SM count from the device, maximum SM clock from the measured peaks file
+    (else nvidia-smi's clocks.max.sm, else the GB300 nominal 2,070 MHz)."""
+    global SM_COUNT, SM_MAX_MHZ, PEAK_SOURCE
+    import torch
+    SM_COUNT = int(torch.cuda.get_device_properties(device).multi_processor_count)
+    mhz = _measured_peaks().get("sm_max_mhz")
+    src = "MEASURED_PEAKS.json sm_max_mhz"
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                                  "-i", str(device)], capture_output=True, text=True, timeout=20).stdout
+            mhz = float(out.strip().splitlines()[0])
+            src = "nvidia-smi clocks.max.sm"
+        except Exception:
+            mhz, src = 2070.0, "GB300 nominal maximum SM clock (fallback)"
+    SM_MAX_MHZ = float(mhz)
+    PEAK_SOURCE = "%d SMs (device) x %.0f MHz (%s)" % (SM_COUNT, SM_MAX_MHZ, src)
+
+
+def fp32_peak():
+    """FP32 lane operations per second (an FMA counting once)."""
+    return SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+
+
+def fp64_peak():
+    """FP64 lane operations per second (an FMA counting once)."""
+    return SM_COUNT * FP64_LANES_PER_SM * SM_MAX_MHZ * 1e6
 
 
 def hbm_peak_gbs():
@@ -103,12 +151,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=20,
+                    help="FP64 evaluations (distinct seeds) for its rate and latency distribution")
+    ap.add_argument("--latency-evals", type=int, default=200,
+                    help="mixed evaluations (distinct seeds) for the latency distribution")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the compact batch / serving / large measurements of the default run")
+    ap.add_argument("--large-fp64", action="store_true",
+                    help="--workload large: also time full FP64 evaluations and compare term by term")
     ap.add_argument("--m", type=int, default=20)
     ap.add_argument("--no-oracle", action="store_true", help="skip the error check and cpu_baseline")
     ap.add_argument("--no-full", action="store_true", help="skip the full-dimensional Genz comparison")
     ap.add_argument("--l2-flush-mb", type=int, default=512)
-    ap.add_argument("--cpu-sample-sites", type=int, default=160)
     ap.add_argument("--workload", default="grid50", choices=["grid50", "batch4096", "serving", "large", "mixture", "grouped", "censored"],
                     help="grid50: the headline line; the others print their own lines")
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -127,12 +181,36 @@ def dist_info():
 
 def alu_roofline(work_ops, seconds, kernel, note=None):
     """The roofline object for FP32-lane work done in `seconds`."""
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    peak = fp32_peak()
     r = {"bound": "alu", "achieved": work_ops / seconds / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-         "frac": work_ops / seconds / peak, "traffic": None, "kernel": kernel}
+         "frac": work_ops / seconds / peak, "traffic": None, "kernel": kernel, "peak_source": PEAK_SOURCE}
     if note:
         r["note"] = note
     return r
+
+
+# FP64-pipe roofline of the FP64 Genz kernel: FP64 operations per Genz step of
+# the formulation the kernel evaluates (an FMA counting once) -- running
+# product 1, lattice-weighted probabilities 2, Phi^{-1} 35 (Phi(-a0) and
+# phi(a0) at the first guess 28: interval map 2, degree-9 polynomial 9, a^2/2
+# as hi + lo 3, exponential 11, products 3; residual, quotient with one
+# correction and Halley factor 7), standardisation 1, Phi 27 (26 + 1 - T) --
+# plus (t + 1) FMAs for the conditional mean of row t + 1.  Compares, min/max,
+# selects and the integer lattice and exponent work are not counted.
+FP64_OPS_STEP = 66
+FP64_OPS_NOTE = ("FP64-pipe lane operations, an FMA counting once; 66 per Genz step + q(q+1)/2 FMAs per "
+                 "point; peak = SMs x 2 FP64 lanes x max SM clock")
+
+
+def fp64_alg_ops_q(q, N, S):
+    if FP64_OPS_STEP is None:
+        return None
+    q = np.asarray(q, dtype=np.float64)
+    return float(N) * S * float(np.sum(q * FP64_OPS_STEP + q * (q + 1) / 2.0))
+
+
+def fp64_alg_ops(D, m, N, S):
+    return fp64_alg_ops_q(np.minimum(np.arange(D), m), N, S)
 
 
 def alg_ops(D, m, N, S):
@@ -193,50 +271,76 @@ def prepare_workload(m, seed=0):
     return inputs.grid50(m=m, seed=seed)
 
 
-def cpu_baseline(prob, n_sample):
-    """The oracle on a bounded, deterministic sample of the workload's terms,
-    scaled by algorithmic work to one full evaluation."""
+def host_cpu():
+    """The host CPU's model name and logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model or "unknown", "logical_cores": os.cpu_count()}
+
+
+def oracle_prepare(prob):
+    """The oracle's own ordering and neighbour search of the workload."""
     import oracle as O
     perm = O.order(prob.sites, O.ORDER_XY)
-    s, u = prob.sites[perm], prob.u[perm]
-    nbr = O.neighbors(s, prob.m)
-    D = s.shape[0]
-    idx = np.unique(np.linspace(0, D - 1, n_sample).astype(np.int64))
-    q = np.minimum(np.arange(D), prob.m)
-    t0 = time.perf_counter()
-    O.vecchia_partials(s, nbr, prob.m, prob.cov, u, prob.N, prob.S, prob.seed, idx=idx)
-    t = time.perf_counter() - t0
-    w_all = float(np.sum(q * (q + 1) / 2.0 + q * ALG_OPS_STEP))
-    w_smp = float(np.sum(q[idx] * (q[idx] + 1) / 2.0 + q[idx] * ALG_OPS_STEP))
-    t_eval = t * w_all / w_smp
-    return {"value": 1.0 / t_eval, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": "%d of %d terms (evenly spaced), N=%d x S=%d, scaled by algorithmic work; %.2f s"
-                      % (len(idx), D, prob.N, prob.S, t)}
+    s, u = np.ascontiguousarray(prob.sites[perm]), np.ascontiguousarray(prob.u[perm])
+    return s, u, O.neighbors(s, prob.m)
 
 
 def run_reference(args):
+    """The oracle on the headline workload.  The K timed steps split one full
+    evaluation (seed 0) into K contiguous slices of terms; step 0 also orders
+    the sites and searches the neighbours, and the last step adds the log-sum,
+    so the steps together are one complete oracle evaluation and their summed
+    time is its measured wall time.  The W warm-up steps evaluate slices of
+    another seed's evaluation, untimed (the oracle keeps no state between
+    calls; they only warm the host caches and the OpenMP pool)."""
+    import oracle as O
     world, rank, _ = dist_info()
     if rank != 0:
         return
     prob = prepare_workload(args.m)
-    for _ in range(max(args.warmup, 0)):
-        pass  # the oracle has no warm-up state beyond its first call
-    n_sample = max(8, args.cpu_sample_sites // 4)
+    D = prob.D
+    K = max(int(args.steps), 1)
+    bounds = [(D * k) // K for k in range(K + 1)]
+    s, u, nbr = oracle_prepare(prob)
+    for k in range(max(args.warmup, 0)):
+        lo, hi = bounds[k % K], bounds[k % K + 1]
+        O.vecchia_partials(s, nbr, prob.m, prob.cov, u, prob.N, prob.S, 1, idx=np.arange(lo, hi))
+    num = np.zeros((D, prob.S))
+    den = np.zeros((D, prob.S))
     times = []
-    cb = None
-    for k in range(args.steps):
-        prob.seed = k
-        cb = cpu_baseline(prob, n_sample)
-        times.append(1.0 / cb["value"])
+    log_p = se = None
+    for k in range(K):
+        t0 = time.perf_counter()
+        if k == 0:
+            s, u, nbr = oracle_prepare(prob)
+        lo, hi = bounds[k], bounds[k + 1]
+        if hi > lo:
+            num[lo:hi], den[lo:hi] = O.vecchia_partials(s, nbr, prob.m, prob.cov, u, prob.N, prob.S, 0,
+                                                        idx=np.arange(lo, hi))
+        if k == K - 1:
+            log_p, se = O.vecchia_reduce(num, den)[:2]
+        times.append(time.perf_counter() - t0)
     t = np.array(times)
-    value = len(t) / t.sum()
+    total = float(t.sum())
+    value = 1.0 / total  # one evaluation in `total` seconds
+    sample = ("one full evaluation (seed 0: ordering, neighbours, all %d terms, log-sum) split into %d "
+              "slices of terms, one per timed step; %.2f s in total" % (D, K, total))
     line = {"impl": "reference", "metric": metric_for(args.m), "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(t.mean()),
+            "steps": K, "warmup": args.warmup, "ms_per_step": 1000.0 * float(t.mean()),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_for(args.m), "precision": "fp64 (oracle)"},
-            "p50_ms": 1000.0 * float(np.percentile(t, 50)), "p99_ms": 1000.0 * float(np.percentile(t, 99)),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                             "sample": cb["sample"]},
+            "data": "synthetic", "config": {"workload": workload_for(args.m), "precision": "fp64 (oracle)",
+                                            "step": "one slice of %d terms of one evaluation" % (D // K)},
+            "eval_s": total, "log_p": log_p, "std_err": se,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -253,6 +357,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
 
+    init_peaks(local)
     prob = prepare_workload(args.m)
     D, m, N, S = prob.D, prob.m, prob.N, prob.S
     ctx = V.Context(local, stream.cuda_stream)
@@ -308,6 +413,9 @@ def run_ours(args):
         total_s = float(t.item())
     value = world * args.steps / total_s
 
+    # latency distributions over distinct seeds: p50/p99 as statistics
+    lat_m, lat_genz_m, _, _ = timed(args.latency_evals, V.MIXED, 100_000) if args.latency_evals > 0 else \
+        (np.zeros(0), np.zeros(0), [], 0.0)
     ms64, genz64, res_fp64 = np.zeros(0), np.zeros(0), []
     if args.fp64_steps > 0:
         ms64, genz64, res_fp64, _ = timed(args.fp64_steps, V.FP64, 0)
@@ -327,8 +435,34 @@ def run_ours(args):
     # roofline of the Genz kernel
     work = alg_ops(D, m, N, S)
     genz_s = float(np.mean(genz_ms)) / 1000.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    peak = fp32_peak()
     achieved = work / genz_s
+
+    def dist(x, seeds):
+        return {"evals": int(len(x)), "seeds": seeds, "p50_ms": float(np.percentile(x, 50)),
+                "p99_ms": float(np.percentile(x, 99)), "mean_ms": float(np.mean(x)),
+                "max_ms": float(np.max(x)), "evals_per_s": 1000.0 / float(np.mean(x))}
+
+    latency = {"how": "CUDA events around each vecchia_log_cdf_unordered call on the library's stream, "
+                      "L2 flushed before each, one seed per evaluation; p99 = 99th percentile of the evals"}
+    if len(lat_m):
+        latency["mixed"] = dist(lat_m, "100000..%d" % (100_000 + len(lat_m) - 1))
+    if len(ms64):
+        latency["fp64"] = dist(ms64, "0..%d" % (len(ms64) - 1))
+    fp64_obj = None
+    if len(ms64):
+        g64 = float(np.mean(genz64)) / 1000.0
+        w64 = fp64_alg_ops(D, m, N, S)
+        fp64_obj = {"value": len(ms64) / (float(ms64.sum()) / 1000.0), "unit": UNIT,
+                    "steps": len(ms64), "p50_ms": float(np.percentile(ms64, 50)),
+                    "p99_ms": float(np.percentile(ms64, 99)), "genz_kernel_ms": g64 * 1000.0}
+        if w64 is not None:
+            fp64_obj["roofline"] = {"bound": "alu", "achieved": w64 / g64 / 1e12, "peak": fp64_peak() / 1e12,
+                                    "unit": "TFLOP/s", "frac": w64 / g64 / fp64_peak(), "traffic": None,
+                                    "kernel": "genz_kernel (fp64)", "kernel_ms": g64 * 1000.0,
+                                    "peak_source": "%d SMs x %d FP64 lanes x %.0f MHz (%s)"
+                                                   % (SM_COUNT, FP64_LANES_PER_SM, SM_MAX_MHZ, PEAK_SOURCE),
+                                    "ops": FP64_OPS_NOTE}
 
     line = {"metric": metric_for(args.m), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
@@ -339,17 +473,16 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "wall_s": wall,
-            "fp64": ({"value": len(ms64) / (float(ms64.sum()) / 1000.0), "unit": UNIT,
-                      "steps": len(ms64), "p50_ms": float(np.percentile(ms64, 50)),
-                      "p99_ms": float(np.percentile(ms64, 99)),
-                      "genz_kernel_ms": float(np.mean(genz64))} if len(ms64) else None),
+            "fp64": fp64_obj,
+            "latency": latency,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": GENZ_TRAFFIC_BYTES_M20 if m == 20 else None,
                          "kernel": "genz_kernel (mixed)", "kernel_ms": genz_s * 1000.0,
                          "ops": "FP32-pipe lane operations, an FMA counting once; %d per Genz step "
                                 "+ q(q+1)/2 FMAs per point; peak = %d SMs x %d lanes x %.0f MHz"
-                                % (ALG_OPS_STEP, SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ)},
+                                % (ALG_OPS_STEP, SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ),
+                         "peak_source": PEAK_SOURCE},
             "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step[V.MIXED] * args.steps,
@@ -391,11 +524,11 @@ def run_ours(args):
                         "(near 1: its shifts disagree by orders of magnitude at this D)")
         line["full_genz"] = full
     if rank == 0 and not args.no_oracle:
+        # the oracle's full evaluation at seed 0 (ordering, neighbours, all
+        # terms, log-sum), timed whole: the error reference and the CPU baseline
         import oracle as O
-        perm = O.order(prob.sites, O.ORDER_XY)
-        s, u = prob.sites[perm], prob.u[perm]
-        nbr = O.neighbors(s, m)
         t0 = time.perf_counter()
+        s, u, nbr = oracle_prepare(prob)
         lp_o, se_o = O.log_cdf(s, nbr, m, prob.cov, u, N, S, 0)
         t_or = time.perf_counter() - t0
         lp_m = res_mixed[0][0]
@@ -404,20 +537,32 @@ def run_ours(args):
             "seed": 0, "oracle_log_p": lp_o, "qmc_se": se_o, "oracle_s": t_or,
             "mixed_abs": abs(lp_m - lp_o), "mixed_tol": 1e-4 * max(1.0, abs(lp_o)),
             "fp64_rel": abs(lp_64 - lp_o) / abs(lp_o), "fp64_tol": 1e-10}
-        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_sample_sites)
+        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                                "sample": "one full evaluation (seed 0: ordering, neighbours, all %d terms, "
+                                          "log-sum), timed whole: %.2f s" % (D, t_or),
+                                "host": host_cpu()}
+    if rank == 0 and world == 1 and not args.no_extra:
+        # compact measurements of the other workloads (each its own context)
+        ctx.close()
+        ctx = None
+        line["batch"] = measure_batch(args, compact=True)
+        line["serving"] = measure_serving(args, compact=True)
+        line["large"] = measure_large(args, compact=True)
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_batch(args):
+def measure_batch(args, compact=False):
     """The batched workload: 4,096 independent problems, D log-uniform in
     [50, 2000], sites uniform in the unit square, maxmin order, exponential
     covariance with range ~ U[0.05, 0.5], u = Phi^{-1}(0.9), m = 20,
     N = 2,048 x S = 8, mixed precision; ordered and searched once, then one
-    plan (resident inputs, CUDA graph) replayed with new seeds each step."""
+    plan (resident inputs, CUDA graph) replayed with new seeds each step.
+    compact: a short tile search (two-point tiles) and three timed replays."""
     import torch
     from concurrent.futures import ThreadPoolExecutor
     import paper_2007_15195_gb300 as V
@@ -425,6 +570,7 @@ def run_batch(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    init_peaks(0)
     stream = torch.cuda.current_stream(dev)
     ctx = V.Context(0, stream.cuda_stream)
     probs = inputs.batch_problems(args.batch_problems)
@@ -438,14 +584,21 @@ def run_batch(args):
         items.append(dict(sites=s, nbr=V.vecchia_neighbors(ctx, s, p.m), m=p.m, cov=p.cov, u=u, N=p.N,
                           S=p.S, seed=p.seed))
     prep_s = time.perf_counter() - t0
-    tuned = autotune.tune(ctx, items, V.MIXED, reps=1, budget_s=60.0)
+    t0 = time.perf_counter()
+    if compact:
+        cands = [(2, 2, 1, 1), (2, 2, 1, 2), (4, 2, 1, 1)]
+        tuned = autotune.tune(ctx, items, V.MIXED, candidates=cands, reps=1, force=True)
+    else:
+        tuned = autotune.tune(ctx, items, V.MIXED, reps=1, budget_s=60.0)
+    tune_s = time.perf_counter() - t0
     plan = V.Plan(ctx, items, V.MIXED)
     n = len(items)
-    for k in range(max(args.warmup, 3)):
+    for k in range(2 if compact else max(args.warmup, 3)):
         plan.run(seeds=np.arange(n, dtype=np.uint64) + 10_000 * (k + 1))
+    steps = 3 if compact else args.steps
     ms = []
     torch.cuda.synchronize(dev)
-    for k in range(args.steps):
+    for k in range(steps):
         t = time.perf_counter()
         lp, se, st = plan.run(seeds=np.arange(n, dtype=np.uint64) + 1_000_000 * (k + 1))
         ms.append(1000.0 * (time.perf_counter() - t))
@@ -454,91 +607,201 @@ def run_batch(args):
     q = [np.minimum(np.arange(int(it["sites"].shape[0])), 20) for it in items]
     work = sum(float(np.sum(qq * ALG_OPS_STEP + qq * (qq + 1) / 2.0)) for qq in q) * 2048 * 8
     genz_s = tuned["ms"] / 1000.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
     line = {"metric": "Vecchia log-CDF evals/s, batched workload (%d problems)" % n,
-            "value": n / (float(ms.mean()) / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
+            "value": n / (float(ms.mean()) / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "ms_per_step": float(ms.mean()), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "batch: %d problems, D log-uniform [50, 2000] (%d sites), maxmin, "
                                    "exponential range U[0.05,0.5], u=Phi^-1(0.9), m=20, N=2048 x S=8"
                                    % (n, sites),
                        "precision": "mixed", "step": "one plan replay (CUDA graph) with new seeds",
-                       "tile": list(tuned["tile"]), "prep_s": prep_s},
+                       "tile": list(tuned["tile"]), "prep_s": prep_s, "tune_s": tune_s},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "all_ok": bool(np.all(st == 0)),
-            "roofline": {"bound": "alu", "achieved": work / genz_s / 1e12, "peak": peak / 1e12,
-                         "unit": "TFLOP/s", "frac": work / genz_s / peak, "traffic": None,
-                         "kernel": "genz_kernel (mixed), autotuned tile", "kernel_ms": tuned["ms"]}}
-    print(json.dumps(line))
+            "roofline": dict(alu_roofline(work, genz_s, "genz_kernel (mixed), tuned tile"),
+                             kernel_ms=tuned["ms"])}
+    if not compact:
+        line["warmup"] = args.warmup
     plan.close()
     ctx.close()
+    return line
 
 
-def run_serving(args):
+def run_batch(args):
+    print(json.dumps(measure_batch(args)))
+
+
+def _serving_run(srv, rate, n_requests, d_hi=50_000.0):
+    from paper_2007_15195_gb300 import inputs
+    from paper_2007_15195_gb300.serve import requests_from_stream
+    reqs = requests_from_stream(inputs.serving_stream(n_requests=n_requests, rate_hz=rate, d_hi=d_hi))
+    stats = srv.run(reqs)
+    stats["work"] = sum(alg_ops(r.D, r.m, 2048, 8) for r in reqs)
+    stats["steps"] = sum(float(np.sum(np.minimum(np.arange(r.D), r.m))) for r in reqs) * 2048 * 8
+    stats["offered_rps"] = rate
+    return stats
+
+
+def _prologue_share(ctx, n_sample=24):
+    """Share of the Genz kernel's time on the serving mix that does not
+    depend on N (each term's covariance block, Cholesky factor and tables,
+    recomputed on every call instead of kept resident): the kernel time at
+    N = 64 over the time at N = 2,048, on a sample of the mix's requests
+    (an upper bound: N = 64 still runs 64 points per shift)."""
+    import torch
+    import paper_2007_15195_gb300 as V
+    from paper_2007_15195_gb300 import inputs
+    dev = torch.device("cuda", ctx.device)
+    stream = inputs.serving_stream(n_requests=n_sample, rate_hz=1.0, workload_seed=7, d_hi=20_000)
+    items = []
+    for rq in stream:
+        p = rq.problem
+        perm = V.vecchia_order(None, p.sites, "xy")
+        s, u = V.vecchia_apply_order(None, perm, p.sites, p.u)
+        s, u = torch.from_numpy(s).to(dev), torch.from_numpy(u).to(dev)
+        items.append(dict(sites=s, nbr=V.vecchia_neighbors(ctx, s, p.m), m=p.m, cov=p.cov, u=u, N=p.N,
+                          S=p.S, seed=p.seed))
+    V.vecchia_set_timing(ctx, True)
+    t = {}
+    for N in (2048, 64):
+        its = [dict(it, N=N) for it in items]
+        V.vecchia_log_cdf_batch(ctx, its, V.MIXED)
+        ts = []
+        for _ in range(3):
+            V.vecchia_log_cdf_batch(ctx, its, V.MIXED)
+            ts.append(V.vecchia_genz_time_ms(ctx))
+        t[N] = float(np.median(ts))
+    return {"genz_ms_N2048": t[2048], "genz_ms_N64": t[64], "share_upper": t[64] / t[2048],
+            "sample": "%d requests of the mix (D <= 20,000), one batch call" % n_sample}
+
+
+def measure_serving(args, compact=False):
     """The serving workload: Poisson arrivals, D log-uniform in [100, 50000],
     m in {10, 20, 30}, Matern range along a random walk in [0.05, 0.5], nu in
     {0.5, 1.5}, sites uniform in the unit square (xy order), N = 2,048 x S = 8,
-    mixed precision, through the continuous-batching loop; one line per rate."""
+    mixed precision, through the continuous-batching loop.  Measured:
+    saturation throughput (2,000 req/s offered, far above what one GPU
+    serves) with its roofline fraction over the run's span (the GPU is busy
+    throughout), p50/p99 at 2,000 req/s, then a short search down from the
+    saturation rate for the highest rate the loop keeps up with (completion
+    rate >= 95 % of the offered rate and p99 <= 1 s), with its p50/p99."""
     import torch
     import paper_2007_15195_gb300 as V
     from paper_2007_15195_gb300 import inputs
     from paper_2007_15195_gb300.serve import Server, requests_from_stream
 
     torch.cuda.set_device(0)
+    init_peaks(0)
     ctx = V.Context(0)
     warm = requests_from_stream(inputs.serving_stream(n_requests=16, rate_hz=1e6, workload_seed=99,
                                                       d_hi=5000))
     srv = Server(ctx, V.MIXED, hbm_budget_bytes=64 << 30, max_active=512, chunk_sites=4096,
                  iter_sites=131072)
     srv.run(warm)
-    for rate in [float(x) for x in args.serve_rates.split(",")]:
-        reqs = requests_from_stream(inputs.serving_stream(n_requests=args.serve_requests, rate_hz=rate))
-        stats = srv.run(reqs)
-        steps = sum(float(np.sum(np.minimum(np.arange(r.D), r.m))) for r in reqs) * 2048 * 8
-        work = sum(alg_ops(r.D, r.m, 2048, 8) for r in reqs)
-        line = {"metric": "Vecchia log-CDF serving: requests/s and p50/p99 latency",
-                "value": stats["throughput_rps"], "unit": "requests/s", "n_gpus": 1,
-                "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "serving: Poisson %.0f req/s, %d requests, D log-uniform [100, 50000], "
-                                       "m in {10,20,30}, Matern nu in {0.5,1.5}, range random walk [0.05,0.5], "
-                                       "N=2048 x S=8, xy order" % (rate, len(reqs)),
-                           "precision": "mixed", "hbm_budget_bytes": srv.budget, "max_active": srv.max_active,
-                           "chunk_sites": srv.chunk, "iter_sites": srv.iter_sites},
-                "offered_rps": rate, "genz_steps_per_s": steps / max(stats["wall_s"], 1e-9),
-                "roofline": alu_roofline(work, max(stats["wall_s"], 1e-9), "genz_kernel (mixed), whole serving run",
-                                         "wall-clock of the run (arrival gaps included)")}
-        line.update({k: stats[k] for k in ("completed", "submitted", "ok", "p50_ms", "p99_ms", "wait_p50_ms",
-                                           "wait_p99_ms", "iterations", "wall_s", "peak_resident_bytes")})
-        print(json.dumps(line))
-        sys.stdout.flush()
+    n_sat = 300 if compact else args.serve_requests
+    sat = _serving_run(srv, 2000.0, n_sat)
+    span = sat["completed"] / max(sat["throughput_rps"], 1e-9)
+    keys = ("completed", "submitted", "ok", "p50_ms", "p99_ms", "wait_p50_ms", "wait_p99_ms", "iterations",
+            "wall_s", "peak_resident_bytes", "throughput_rps", "offered_rps")
+    out = {"metric": "Vecchia log-CDF serving: requests/s and p50/p99 latency",
+           "value": sat["throughput_rps"], "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "serving: Poisson arrivals, D log-uniform [100, 50000], m in {10,20,30}, "
+                                  "Matern nu in {0.5,1.5}, range random walk [0.05,0.5], N=2048 x S=8, xy order",
+                      "precision": "mixed", "hbm_budget_bytes": srv.budget, "max_active": srv.max_active,
+                      "chunk_sites": srv.chunk, "iter_sites": srv.iter_sites},
+           "saturation": dict({k: sat[k] for k in keys},
+                              genz_steps_per_s=sat["steps"] / span,
+                              roofline=alu_roofline(sat["work"], span, "genz_kernel (mixed), saturated serving run",
+                                                    "algorithmic work of the completed requests over the span "
+                                                    "from the first arrival to the last completion; the GPU "
+                                                    "is busy throughout at saturation"))}
+    n_search = 150 if compact else max(args.serve_requests // 2, 150)
+    search = []
+    best = None
+    for frac in (0.85, 0.7, 0.55, 0.4, 0.25):
+        rate = max(1.0, frac * sat["throughput_rps"])
+        r = _serving_run(srv, rate, n_search)
+        done_rate = r["completed"] / max(r["wall_s"], 1e-9)
+        ok = r["p99_ms"] is not None and r["p99_ms"] <= 1000.0 and r["throughput_rps"] >= 0.95 * rate
+        search.append({"offered_rps": rate, "throughput_rps": r["throughput_rps"], "p50_ms": r["p50_ms"],
+                       "p99_ms": r["p99_ms"], "completed": r["completed"], "bounded": ok,
+                       "completion_rate": done_rate})
+        if ok:
+            best = {k: r[k] for k in keys}
+            break
+    out["rate_search"] = search
+    out["highest_bounded"] = best
     srv.close()
+    out["factors_recomputed"] = _prologue_share(ctx)
     ctx.close()
+    return out
 
 
-def run_large(args):
+def run_serving(args):
+    print(json.dumps(measure_serving(args)))
+
+
+def _term_conditioning(s, nbr, m, cov):
+    """Per term: L_qq^2 / Sigma_qq of its block (the last variable's
+    conditional variance fraction given its neighbours; near 0 for a site
+    nearly duplicated by a neighbour), from numpy's Cholesky of each block."""
+    from paper_2007_15195_gb300 import inputs
+    D = s.shape[0]
+    out = np.ones(D)
+    kind, var, rng_, nu = cov[0], cov[1], cov[2], cov[3]
+
+    def k(h):
+        r = h / rng_
+        if kind == 1 and nu == 1.5:
+            return var * (1.0 + np.sqrt(3.0) * r) * np.exp(-np.sqrt(3.0) * r)
+        if kind == 1 and nu == 2.5:
+            return var * (1.0 + np.sqrt(5.0) * r + 5.0 * r * r / 3.0) * np.exp(-np.sqrt(5.0) * r)
+        return var * np.exp(-r)
+
+    for d in range(2, m + 2):
+        q = d - 1
+        idx = np.arange(D)[np.minimum(np.arange(D), m) == q]
+        if idx.size == 0:
+            continue
+        blk = np.concatenate([nbr[idx, :q], idx[:, None]], axis=1)
+        pts = s[blk]
+        h = np.sqrt(((pts[:, :, None, :] - pts[:, None, :, :]) ** 2).sum(-1))
+        L = np.linalg.cholesky(k(h))
+        out[idx] = L[:, -1, -1] ** 2 / var
+    return out
+
+
+def measure_large(args, compact=False):
     """The large workload: D = 100,000 uniform sites, exact maxmin order,
     Matern nu in {0.5, 1.5} with range 0.05, u ~ U[0, 2], m = 30,
-    N = 8,192 x S = 16: ordering (host), neighbour search and the mixed
-    log-CDF timed separately; the FP64 path on a 10,000-site ordered prefix
-    (its per-step rate scales to the full problem)."""
+    N = 8,192 x S = 16: ordering (device), neighbour search and the mixed
+    log-CDF timed separately.  --large-fp64: also full FP64 evaluations at
+    full size, the mixed error against them, term by term and binned by each
+    term's conditioning."""
     import torch
     import paper_2007_15195_gb300 as V
     from paper_2007_15195_gb300 import inputs
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    init_peaks(0)
     ctx = V.Context(0)
     V.vecchia_set_timing(ctx, True)
+    per_nu = []
     for nu in (1.5, 0.5):
         prob = inputs.large(nu=nu)
-        t0 = time.perf_counter()
-        perm_h = V.vecchia_order(None, prob.sites, "maxmin")  # host, all cores
-        t_order_host = time.perf_counter() - t0
+        t_order_host, same_order = None, None
+        if not compact:
+            t0 = time.perf_counter()
+            perm_h = V.vecchia_order(None, prob.sites, "maxmin")  # host, all cores
+            t_order_host = time.perf_counter() - t0
         V.vecchia_order(ctx, prob.sites[:2048], "maxmin")  # warm-up
         t0 = time.perf_counter()
         perm = V.vecchia_order(ctx, prob.sites, "maxmin")  # device
         t_order = time.perf_counter() - t0
-        same_order = bool(np.array_equal(perm, perm_h))
+        if not compact:
+            same_order = bool(np.array_equal(perm, perm_h))
         s, u = V.vecchia_apply_order(None, perm, prob.sites, prob.u)
         ds, du = torch.from_numpy(s).to(dev), torch.from_numpy(u).to(dev)
         nbr = V.vecchia_neighbors(ctx, ds, prob.m)
@@ -546,41 +809,68 @@ def run_large(args):
         t0 = time.perf_counter()
         for _ in range(3):
             nbr = V.vecchia_neighbors(ctx, ds, prob.m)
+        torch.cuda.synchronize()
         t_knn = (time.perf_counter() - t0) / 3
         V.vecchia_log_cdf(ctx, ds, nbr, prob.m, prob.cov, du, prob.N, prob.S, 99, V.MIXED)
         ms, genz = [], []
-        for k in range(max(args.steps // 10, 2)):
+        for k in range(2 if compact else max(args.steps // 10, 2)):
             t0 = time.perf_counter()
             lp, se = V.vecchia_log_cdf(ctx, ds, nbr, prob.m, prob.cov, du, prob.N, prob.S, k, V.MIXED)
             ms.append(1000.0 * (time.perf_counter() - t0))
             genz.append(V.vecchia_genz_time_ms(ctx))
-        K = 10_000
-        pre = (ds[:K].contiguous(), du[:K].contiguous(), nbr[:K].contiguous())
-        t0 = time.perf_counter()
-        lp64, se64 = V.vecchia_log_cdf(ctx, pre[0], pre[2], prob.m, prob.cov, pre[1], prob.N, prob.S, 0, V.FP64)
-        t64 = time.perf_counter() - t0
         q = np.minimum(np.arange(prob.D), prob.m).astype(np.float64)
         steps = float(q.sum()) * prob.N * prob.S
-        steps_pre = float(q[:K].sum()) * prob.N * prob.S
         work = float(np.sum(q * ALG_OPS_STEP + q * (q + 1) / 2.0)) * prob.N * prob.S
-        peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
         genz_s = float(np.median(genz)) / 1000.0
-        line = {"metric": "Vecchia log-CDF evals/s, large workload (D=100,000, m=30)",
-                "value": 1000.0 / float(np.mean(ms)), "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-                "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "large: D=100000 uniform, maxmin, Matern nu=%g range 0.05, u~U[0,2], "
-                                       "m=30, N=8192 x S=16" % nu, "precision": "mixed"},
-                "ms_per_eval": float(np.mean(ms)), "log_p": lp, "std_err": se, "order_s": t_order,
-                "order_host_s": t_order_host, "order_device_equals_host": same_order,
-                "neighbors_ms": 1000.0 * t_knn, "genz_steps": steps,
-                "fp64_prefix": {"sites": K, "s": t64, "log_p": lp64,
-                                "est_full_s": t64 * steps / steps_pre},
-                "roofline": {"bound": "alu", "achieved": work / genz_s / 1e12, "peak": peak / 1e12,
-                             "unit": "TFLOP/s", "frac": work / genz_s / peak, "traffic": None,
-                             "kernel": "genz_kernel (mixed)", "kernel_ms": genz_s * 1000.0}}
-        print(json.dumps(line))
-        sys.stdout.flush()
+        row = {"nu": nu, "evals_per_s": 1000.0 / float(np.mean(ms)), "ms_per_eval": float(np.mean(ms)),
+               "log_p": lp, "std_err": se, "order_s": t_order, "neighbors_ms": 1000.0 * t_knn,
+               "genz_steps": steps,
+               "roofline": dict(alu_roofline(work, genz_s, "genz_kernel (mixed)"), kernel_ms=genz_s * 1000.0)}
+        if t_order_host is not None:
+            row["order_host_s"] = t_order_host
+            row["order_device_equals_host"] = same_order
+        if args.large_fp64 and not compact:
+            # full-size FP64 evaluation (seed 0), term by term beside the mixed one
+            t0 = time.perf_counter()
+            lp64, se64, terms64, _, _ = V.vecchia_log_cdf_terms(ctx, ds, nbr, prob.m, prob.cov, du, prob.N,
+                                                                prob.S, 0, V.FP64)
+            t64 = time.perf_counter() - t0
+            g64 = V.vecchia_genz_time_ms(ctx) / 1000.0
+            lpm, sem, termsm, _, _ = V.vecchia_log_cdf_terms(ctx, ds, nbr, prob.m, prob.cov, du, prob.N,
+                                                             prob.S, 0, V.MIXED)
+            d = np.abs(terms64.cpu().numpy() - termsm.cpu().numpy())
+            cond = _term_conditioning(s, nbr.cpu().numpy(), prob.m, prob.cov)
+            edges = [0.0, 1e-4, 1e-3, 1e-2, 1e-1, 1.0001]
+            bins = []
+            for lo, hi in zip(edges[:-1], edges[1:]):
+                sel = (cond >= lo) & (cond < hi)
+                if sel.any():
+                    bins.append({"cond_var_frac": [lo, min(hi, 1.0)], "terms": int(sel.sum()),
+                                 "max_abs_dterm": float(d[sel].max()), "mean_abs_dterm": float(d[sel].mean())})
+            w64 = fp64_alg_ops_q(q, prob.N, prob.S)
+            row["fp64"] = {"s_per_eval": t64, "evals_per_s": 1.0 / t64, "log_p": lp64, "std_err": se64,
+                           "genz_kernel_s": g64,
+                           "roofline": None if w64 is None else
+                                       {"bound": "alu", "achieved": w64 / g64 / 1e12, "peak": fp64_peak() / 1e12,
+                                        "unit": "TFLOP/s", "frac": w64 / g64 / fp64_peak(), "traffic": None,
+                                        "kernel": "genz_kernel (fp64)", "ops": FP64_OPS_NOTE},
+                           "mixed_vs_fp64": {"abs": abs(lpm - lp64), "tol": 1e-4 * max(1.0, abs(lp64)),
+                                             "max_abs_dterm": float(d.max()), "by_conditioning": bins,
+                                             "cond": "L_qq^2 / Sigma_qq of each term's block"}}
+        per_nu.append(row)
     ctx.close()
+    head = per_nu[0]
+    line = {"metric": "Vecchia log-CDF evals/s, large workload (D=100,000, m=30)",
+            "value": head["evals_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "large: D=100000 uniform, maxmin (device), Matern nu in {1.5, 0.5} range 0.05, "
+                                   "u~U[0,2], m=30, N=8192 x S=16", "precision": "mixed (value: nu=1.5)"},
+            "per_nu": per_nu}
+    return line
+
+
+def run_large(args):
+    print(json.dumps(measure_large(args)))
 
 
 def run_mixture(args):
@@ -613,7 +903,7 @@ def run_mixture(args):
         genz.append(V.vecchia_genz_time_ms(ctx))
     ms = np.array(ms)
     work = n * alg_ops(prob.D, prob.m, prob.N, prob.S)
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    peak = fp32_peak()
     genz_s = float(np.median(genz)) / 1000.0
     line = {"metric": "scale-mixture log G evals/s (D=2500, m=20, %d nodes)" % n,
             "value": 1000.0 / float(ms.mean()), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
@@ -653,7 +943,7 @@ def run_grouped(args):
     perm = V.vecchia_order(None, prob.sites, prob.order)
     s, u = V.vecchia_apply_order(None, perm, prob.sites, prob.u)
     ds, du = torch.from_numpy(s).to(dev), torch.from_numpy(u).to(dev)
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    peak = fp32_peak()
     m = 5
     rows = []
     head = None
@@ -702,7 +992,7 @@ def run_grouped(args):
                                    "N=2048 x S=8, xy order, p in {2,5,10}, m=5", "precision": "mixed",
                        "step": "vecchia_grouped_log_cdf on resident device arrays"},
             "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "configs": rows,
-            "roofline": dict(alu_roofline(head["alu_frac"] * SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6, 1.0,
+            "roofline": dict(alu_roofline(head["alu_frac"] * fp32_peak(), 1.0,
                                           "genz_kernel (mixed), p=5 nearest"))}
     print(json.dumps(line))
     ctx.close()
