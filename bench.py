@@ -746,7 +746,6 @@ def _term_conditioning(s, nbr, m, cov):
     """Per term: L_qq^2 / Sigma_qq of its block (the last variable's
     conditional variance fraction given its neighbours; near 0 for a site
     nearly duplicated by a neighbour), from numpy's Cholesky of each block."""
-    from paper_2007_15195_gb300 import inputs
     D = s.shape[0]
     out = np.ones(D)
     kind, var, rng_, nu = cov[0], cov[1], cov[2], cov[3]
@@ -761,14 +760,14 @@ def _term_conditioning(s, nbr, m, cov):
 
     for d in range(2, m + 2):
         q = d - 1
-        idx = np.arange(D)[np.minimum(np.arange(D), m) == q]
-        if idx.size == 0:
-            continue
-        blk = np.concatenate([nbr[idx, :q], idx[:, None]], axis=1)
-        pts = s[blk]
-        h = np.sqrt(((pts[:, :, None, :] - pts[:, None, :, :]) ** 2).sum(-1))
-        L = np.linalg.cholesky(k(h))
-        out[idx] = L[:, -1, -1] ** 2 / var
+        all_idx = np.arange(D)[np.minimum(np.arange(D), m) == q]
+        for c0 in range(0, all_idx.size, 8192):
+            idx = all_idx[c0:c0 + 8192]
+            blk = np.concatenate([nbr[idx, :q], idx[:, None]], axis=1)
+            pts = s[blk]
+            h = np.sqrt(((pts[:, :, None, :] - pts[:, None, :, :]) ** 2).sum(-1))
+            L = np.linalg.cholesky(k(h))
+            out[idx] = L[:, -1, -1] ** 2 / var
     return out
 
 

@@ -356,8 +356,7 @@ int vecchia_shifts(uint64_t seed, int S, int dim, double* delta);
  * (bucket b holds problems whose largest term has d <= 9, 13, 17, 21, 25,
  * 29, 32, 48, 64 variables for b = 0..8 -- d = m + 1, or m + p for groups of
  * p; -1 = all): warps per CTA (1..16; at most 8 above 32 variables), points
- * per lane per pass (1, 2 or 4; 4 applies to blocks of up to 21 variables and
- * falls back to 2 above; FP64 and blocks above 32 variables use 1),
+ * per lane per pass (1 or 2; FP64 and blocks above 32 variables use 1),
  * lattice slices per shift spread over a CTA's warps (>= 1), shift groups per
  * term spread over CTAs (1..VECCHIA_MAX_S).  Tiles change only the launch
  * shape; results are identical up to the order of the final FP64 sums. */

@@ -1888,7 +1888,7 @@ int vecchia_set_tile(vecchia_ctx* c, int precision, int bucket, int warps, int p
     if (!c || (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) || bucket < -1 ||
         bucket >= vk::kNumBuckets)
         return VECCHIA_ERR_ARG;
-    if (warps < 1 || warps > 16 || (points != 1 && points != 2 && points != 4) || slices < 1 ||
+    if (warps < 1 || warps > 16 || (points != 1 && points != 2) || slices < 1 ||
         groups < 1 || groups > VECCHIA_MAX_S)
         return VECCHIA_ERR_ARG;
     const int b0 = bucket < 0 ? 0 : bucket, b1 = bucket < 0 ? vk::kNumBuckets - 1 : bucket;

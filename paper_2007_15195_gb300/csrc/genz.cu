@@ -33,7 +33,6 @@
 #include <tuple>
 
 #include "cov.cuh"
-#include "f32x2.h"
 #include "special_f32.h"
 #include "special_f64.h"
 #include "vk_internal.h"
@@ -70,9 +69,6 @@ struct GenzSmem {
     // mean by 1/L_vv (diag), one rounding more than the definition's division.
     static constexpr int LS = (DMAX + 3) & ~3;  // row stride: 16-byte aligned rows
     __align__(16) T Lup[DMAX][LS];
-    // MIXED with four points per lane: (-Lup[t][r], -Lup[t][r]), the
-    // coefficient of both points of a pair in one 64-bit load
-    __align__(16) float2 Ln2[(MIXED && DMAX <= 21) ? DMAX : 1][LS];
     __align__(16) T Lz[DMAX];
     __align__(16) T up[DMAX];  // MIXED: u_v / L_vv;  FP64: u_v
     uint32_t gl[DMAX];         // FP64: g_t;  MIXED: round(g_t 2^32 / N)
@@ -339,47 +335,6 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
     }
 }
 
-// Four points per lane as two f32x2 pairs (points k, k + 32 | k + 64, k + 96):
-// each pair's whole step -- the lattice-weighted probabilities, both
-// polynomials, the products and the conditional-mean updates -- in packed
-// instructions, element by element the arithmetic of fast_step (bit-identical
-// values).  The two pairs are independent dependency chains; the lattice
-// coordinates, special-function-unit calls and selects stay per point, and
-// one full-warp vote per step decides the tail pieces for all four points.
-template <int DMAX, int W, bool FIRST>
-__device__ __forceinline__ void fast_step4(const GenzSmem<DMAX, true>& sm, const float4* sc, int t,
-                                           x2::f2 (&R)[2][DMAX - 1], x2::f2 (&e)[2], x2::f2 (&ec)[2],
-                                           x2::f2 (&g)[2], const uint32_t (&kk)[4]) {
-    const x2::f2* ln = reinterpret_cast<const x2::f2*>(sm.Ln2[t]);
-    const float4 c = sc[t];
-    const x2::f2 nlz = x2::splat(c.x);
-    const uint32_t G = __float_as_uint(c.y), Dt = __float_as_uint(c.z);
-    x2::f2 pp[2], qq[2], f[2];
-    bool tl[4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        if (!FIRST) g[h] = x2::mul(g[h], e[h]);  // g = e_1 ... e_t
-        const uint32_t X0 = kk[2 * h] * G + Dt, X1 = kk[2 * h + 1] * G + Dt;
-        const x2::f2 w = x2::pack(__fmul_rn(fabsf(__int2float_rn((int32_t)X0)), 0x1p-31f),
-                                  __fmul_rn(fabsf(__int2float_rn((int32_t)X1)), 0x1p-31f));
-        pp[h] = x2::mul(w, e[h]);
-        qq[h] = x2::fma(w, ec[h], x2::sub(x2::splat(1.0f), w));
-        f[h] = special::phiinv_central2(pp[h], qq[h], tl[2 * h], tl[2 * h + 1]);
-    }
-    if (__any_sync(0xffffffffu, tl[0] || tl[1] || tl[2] || tl[3])) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) f[h] = special::phiinv_tail2(pp[h], qq[h], tl[2 * h], tl[2 * h + 1], f[h]);
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const x2::f2 y = x2::mul(x2::sub(pp[h], qq[h]), f[h]);
-        const x2::f2 z = x2::fma(nlz, y, R[h][0]);
-#pragma unroll
-        for (int r = 0; r < W; ++r) R[h][r] = x2::fma(ln[r], y, R[h][r + 1]);
-        special::phi_pair_fast2(z, e[h], ec[h]);
-    }
-}
-
 // Width step between phases: 4 up to 21 variables; 6 above, where fewer
 // copies of the step body (instruction cache) beat the extra padding FMAs
 // (measured: m = 30 5.7 % faster, m <= 16 0.7 % slower with 6).
@@ -411,22 +366,6 @@ __device__ __forceinline__ void fast_phases(const GenzSmem<DMAX, true>& sm, cons
     if constexpr (WN > 0) fast_phases<DMAX, P, WN, CAPTURE>(sm, sc, t_end, q, cut, R, e, ec, g, gd, kk);
 }
 
-template <int DMAX, int W, bool CAPTURE>
-__device__ __forceinline__ void fast_phases4(const GenzSmem<DMAX, true>& sm, const float4* sc, int t, int q,
-                                             int cut, x2::f2 (&R)[2][DMAX - 1], x2::f2 (&e)[2], x2::f2 (&ec)[2],
-                                             x2::f2 (&g)[2], x2::f2 (&gd)[2], const uint32_t (&kk)[4]) {
-    constexpr int WN = W - phase_step(DMAX);
-    const int t_end = (WN > 0) ? max(t, min(q, q - 1 - WN)) : q;
-    for (int tt = t; tt < t_end; ++tt) {
-        if (CAPTURE && tt == cut) {
-            gd[0] = g[0];
-            gd[1] = g[1];
-        }
-        fast_step4<DMAX, W, false>(sm, sc, tt, R, e, ec, g, kk);
-    }
-    if constexpr (WN > 0) fast_phases4<DMAX, WN, CAPTURE>(sm, sc, t_end, q, cut, R, e, ec, g, gd, kk);
-}
-
 template <int DMAX, int P, bool CAPTURE>
 __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm, int q, int c, int s,
                                                  int max_S, int64_t k_begin, int64_t k_end,
@@ -441,45 +380,6 @@ __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm,
     __syncwarp();
     const float e0f = (float)sm.e0, ec0f = (float)sm.ec0;
     Kahan32 kn, kd;
-    if constexpr (P == 4) {
-        for (int64_t kb = k_begin; kb < k_end; kb += 128) {
-            x2::f2 R[2][DMAX - 1];
-            uint32_t kk[4];
-            bool valid[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int64_t k = kb + p * 32 + lane;
-                valid[p] = k < k_end;
-                kk[p] = (uint32_t)(valid[p] ? k : k_begin);
-            }
-#pragma unroll
-            for (int r = 0; r < DMAX - 1; ++r) R[0][r] = R[1][r] = x2::splat(sm.up[1 + r]);
-            x2::f2 e[2], ec[2], g[2], gd[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                e[h] = x2::splat(e0f);
-                ec[h] = x2::splat(ec0f);
-                g[h] = gd[h] = x2::splat(1.0f);  // c = 1: e_0 alone (factored out)
-            }
-            fast_step4<DMAX, W0, true>(sm, sc, 0, R, e, ec, g, kk);  // q >= 1: step 0 at full width
-            fast_phases4<DMAX, W0, CAPTURE>(sm, sc, 1, q, c, R, e, ec, g, gd, kk);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float g0, g1, e0, e1, d0, d1;
-                x2::unpack(g[h], g0, g1);
-                x2::unpack(e[h], e0, e1);
-                x2::unpack(gd[h], d0, d1);
-                if (valid[2 * h]) {
-                    kd.add(CAPTURE ? d0 : g0);
-                    kn.add(__fmul_rn(g0, e0));
-                }
-                if (valid[2 * h + 1]) {
-                    kd.add(CAPTURE ? d1 : g1);
-                    kn.add(__fmul_rn(g1, e1));
-                }
-            }
-        }
-    } else {
     for (int64_t kb = k_begin; kb < k_end; kb += 32 * P) {
         float R[P][DMAX - 1], e[P], ec[P], g[P], gd[P];
         uint32_t kk[P];
@@ -505,7 +405,6 @@ __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm,
                 kn.add(__fmul_rn(g[p], e[p]));
             }
         }
-    }
     }
     acc_num += kn.value();
     acc_den += kd.value();
@@ -656,14 +555,10 @@ constexpr int kModeFP64 = 0, kModeFast = 1, kModeSafe = 2;
 #ifndef VK_CAP_P2_LARGE
 #define VK_CAP_P2_LARGE 128
 #endif
-#ifndef VK_CAP_P4
-#define VK_CAP_P4 168
-#endif
 __host__ __device__ constexpr int reg_cap(int dmax, int p, int mode) {
     return dmax > 32            ? (mode == kModeFast ? 128 : 255)
            : mode != kModeFast ? 128
            : p == 1            ? (dmax <= 16 ? VK_CAP_P1_SMALL : VK_CAP_P1_LARGE)
-           : p == 4            ? VK_CAP_P4
                                : (dmax <= 16 ? VK_CAP_P2_SMALL : VK_CAP_P2_LARGE);
 }
 __host__ __device__ constexpr int max_threads(int dmax, int p, int mode) {
@@ -839,7 +734,6 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
                         val = sm.A[v][t];
                 }
                 sm.Lup[t][r] = val;
-                if constexpr (MIXED && DMAX <= 21) sm.Ln2[t][r] = make_float2(-(float)val, -(float)val);
             }
             for (int v = threadIdx.x; v < DMAX; v += blockDim.x) {
                 T val = (T)0, lz = (T)0;
@@ -1184,24 +1078,16 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
         if (t.points >= 2)                                                                       \
             return launch_one<DM, 2, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);    \
         return launch_one<DM, 1, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);
-#define VK_CASE4(IDX, DM)                                                                        \
-    case IDX:                                                                                    \
-        if (!mixed) return launch_one<DM, 1, kModeFP64>(VK_ARGS, nullptr, nullptr, st);           \
-        if (t.points >= 4)                                                                       \
-            return launch_one<DM, 4, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);    \
-        if (t.points >= 2)                                                                       \
-            return launch_one<DM, 2, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);    \
-        return launch_one<DM, 1, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);
 #define VK_CASE1(IDX, DM)                                                                        \
     case IDX:                                                                                    \
         if (!mixed) return launch_one<DM, 1, kModeFP64>(VK_ARGS, nullptr, nullptr, st);           \
         return launch_one<DM, 1, kModeFast>(VK_ARGS, fallback_count, fallback_items, st);
     static_assert(kNumBuckets == 9, "bucket table");
     switch (bucket) {
-        VK_CASE4(0, 9)
-        VK_CASE4(1, 13)
-        VK_CASE4(2, 17)
-        VK_CASE4(3, 21)
+        VK_CASE(0, 9)
+        VK_CASE(1, 13)
+        VK_CASE(2, 17)
+        VK_CASE(3, 21)
         VK_CASE(4, 25)
         VK_CASE(5, 29)
         VK_CASE(6, 32)
@@ -1211,7 +1097,6 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
             return cudaErrorInvalidValue;
     }
 #undef VK_CASE
-#undef VK_CASE4
 #undef VK_CASE1
 #undef VK_ARGS
 }

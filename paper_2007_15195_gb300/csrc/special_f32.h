@@ -14,7 +14,6 @@
 // next: every kernel variant computes bit-identical values.
 #pragma once
 
-#include "f32x2.h"
 #include "special_f32.cuh"
 
 namespace vk {
@@ -145,52 +144,6 @@ __device__ __forceinline__ float phiinv_with_tail(float p, float q, bool tail, f
 }
 __device__ __forceinline__ float phiinv_finish(float p, float q, float f) {
     return __fmul_rn(__fsub_rn(p, q), f);
-}
-
-// The pair forms: two lattice points in one f32x2 register, element by element
-// the arithmetic of the scalar forms above (the same operations with the same
-// rounding, so the values are bit-identical), the products, sums and
-// polynomials in packed instructions.
-
-// Central factor of Phi^{-1} for both points (phiinv_central), and whether
-// each needs the tail pieces.
-__device__ __forceinline__ x2::f2 phiinv_central2(x2::f2 p, x2::f2 q, bool& tail0, bool& tail1) {
-    float a, b;
-    x2::unpack(x2::mul(p, q), a, b);
-    const float L0 = lg2(a), L1 = lg2(b);
-    tail0 = !(L0 > kINV1Lmin);
-    tail1 = !(L1 > kINV1Lmin);
-    return x2::horner(kINV1C, x2::fma(x2::pack(L0, L1), x2::splat(kINV1LA), x2::splat(kINV1LB)));
-}
-
-// The tail factor where a point needs it (phiinv_with_tail on each element).
-__device__ __forceinline__ x2::f2 phiinv_tail2(x2::f2 p, x2::f2 q, bool tail0, bool tail1, x2::f2 f) {
-    float p0, p1, q0, q1, f0, f1;
-    x2::unpack(p, p0, p1);
-    x2::unpack(q, q0, q1);
-    x2::unpack(f, f0, f1);
-    return x2::pack(phiinv_with_tail(p0, q0, tail0, f0), phiinv_with_tail(p1, q1, tail1, f1));
-}
-
-// Phi(z) and 1 - Phi(z) for both points (phi_pair_fast).
-__device__ __forceinline__ void phi_pair_fast2(x2::f2 z, x2::f2& e, x2::f2& ec) {
-    float z0, z1;
-    x2::unpack(z, z0, z1);
-    const x2::f2 az = x2::pack(fabsf(z0), fabsf(z1));
-    float d0, d1;
-    x2::unpack(x2::fma(az, x2::splat(kKt), x2::splat(1.0f)), d0, d1);
-    const x2::f2 t = x2::pack(rcp(d0), rcp(d1));
-    const x2::f2 a = x2::fma(x2::mul(az, x2::splat(-0.5f * kLog2e)), az,
-                             x2::horner(kPHIC, x2::fma(t, x2::splat(kPHIA), x2::splat(kPHIB))));
-    float a0, a1;
-    x2::unpack(a, a0, a1);
-    const x2::f2 tail = x2::mul(t, x2::pack(ex2(a0), ex2(a1)));
-    const x2::f2 omt = x2::sub(x2::splat(1.0f), tail);
-    float t0, t1, o0, o1;
-    x2::unpack(tail, t0, t1);
-    x2::unpack(omt, o0, o1);
-    e = x2::pack(z0 < 0.0f ? t0 : o0, z1 < 0.0f ? t1 : o1);
-    ec = x2::pack(z0 < 0.0f ? o0 : t0, z1 < 0.0f ? o1 : t1);
 }
 
 // Phi^{-1}(r) for r = 2^lr2 < 2^-64 (log2 input).

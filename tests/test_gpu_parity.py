@@ -301,8 +301,7 @@ def test_tiles_change_only_sum_order(ctx):
     for prec in (B.FP64, B.MIXED):
         B.vecchia_reset_tiles(ctx)
         ref = B.vecchia_log_cdf(ctx, s, nbr, 20, prob.cov, u, prob.N, prob.S, 1, prec)
-        for warps, points, slices, groups in [(1, 1, 1, 1), (8, 2, 1, 8), (4, 2, 4, 2), (16, 1, 2, 3), (4, 4, 1, 1),
-                                              (2, 4, 1, 3), (4, 4, 2, 2)]:
+        for warps, points, slices, groups in [(1, 1, 1, 1), (8, 2, 1, 8), (4, 2, 4, 2), (16, 1, 2, 3), (2, 2, 1, 3)]:
             B.vecchia_set_tile(ctx, prec, -1, warps, points, slices, groups)
             lp, se = B.vecchia_log_cdf(ctx, s, nbr, 20, prob.cov, u, prob.N, prob.S, 1, prec)
             if slices == 1:  # same points per lane in the same order: bit-identical
@@ -312,21 +311,21 @@ def test_tiles_change_only_sum_order(ctx):
         B.vecchia_reset_tiles(ctx)
 
 
-@pytest.mark.parametrize("m,N", [(3, 1000), (8, 77), (12, 4096), (16, 129), (20, 1000)])
-def test_four_points_per_lane_equal_one(ctx, m, N):
-    """Four points per lane (two f32x2 pairs, blocks of up to 21 variables)
-    compute element by element the arithmetic of one point per lane: the
-    per-shift partial means must agree bit for bit, with ragged point counts."""
+@pytest.mark.parametrize("m,N", [(3, 1000), (8, 77), (12, 4096), (16, 129), (20, 1000), (28, 333)])
+def test_two_points_per_lane_equal_one(ctx, m, N):
+    """Two points per lane compute, point by point, the arithmetic of one
+    point per lane: the per-shift partial means agree bit for bit, with point
+    counts that leave the last pass of a lane ragged."""
     prob = inputs.small_random(300, 14 + m, m=m, N=N, S=4)
     _, s, u, nbr = oracle_prepare(prob)
     out = {}
-    for pts in (1, 4):
+    for pts in (1, 2):
         B.vecchia_set_tile(ctx, B.MIXED, -1, 4, pts, 1, 1)
         out[pts] = B.vecchia_log_cdf_terms(ctx, s, nbr, m, prob.cov, u, prob.N, prob.S, 2, B.MIXED)
     B.vecchia_reset_tiles(ctx)
-    assert out[1][0] == out[4][0] and out[1][1] == out[4][1]
-    assert np.array_equal(np.asarray(out[1][3]), np.asarray(out[4][3]))
-    assert np.array_equal(np.asarray(out[1][4]), np.asarray(out[4][4]))
+    assert out[1][0] == out[2][0] and out[1][1] == out[2][1]
+    assert np.array_equal(np.asarray(out[1][3]), np.asarray(out[2][3]))
+    assert np.array_equal(np.asarray(out[1][4]), np.asarray(out[2][4]))
 
 
 def test_mixed_underflow_falls_back_to_log_space(ctx):

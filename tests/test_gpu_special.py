@@ -96,10 +96,14 @@ def test_phi64_relative_error_of_the_smaller_tail(ctx):
 
 
 def test_phi64_below_the_normal_range(ctx):
-    x = np.linspace(-38.4, -37.6, 801)  # Phi(x) between ~1e-323 and 2^-1022
+    # Phi(x) between ~6e-323 and 2^-1022 (subnormal results).  scipy's ndtr
+    # flushes to 0 below x ~ -37.7; libm's erfc (the oracle's Phi) does not.
+    import oracle as O
+    x = np.linspace(-38.4, -37.6, 801)
     e = _run64(ctx, 0, x)
-    ref = special.ndtr(x)
-    assert np.all(np.abs(e - ref) <= 1e-3 * ref + 5e-324)
+    ref = np.array([O.Phi(v) for v in x])
+    assert np.all(ref > 0)
+    assert np.all(np.abs(e - ref) <= 1e-12 * ref + 1e-323)
 
 
 def test_quantile64_from_either_tail(ctx):
@@ -111,7 +115,9 @@ def test_quantile64_from_either_tail(ctx):
     assert np.max(err[p < 0.4]) < 2e-14, (np.max(err), p[np.argmax(err)])
     assert np.max(np.abs(y - ref)[p >= 0.4]) < 1e-15
     yu = _run64(ctx, 3, p)  # Phi^{-1}(1 - p) from q = p
-    assert np.max(np.abs(yu + ref) / np.maximum(np.abs(ref), 1e-300)) < 2e-14
+    erru = np.abs(yu + ref) / np.maximum(np.abs(ref), 1e-300)
+    assert np.max(erru[p < 0.4]) < 2e-14
+    assert np.max(np.abs(yu + ref)[p >= 0.4]) < 1e-15
 
 
 def test_quantile64_clamps_at_2_pow_minus_1000(ctx):
