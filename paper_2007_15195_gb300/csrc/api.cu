@@ -415,7 +415,7 @@ int prepare(vecchia_ctx* c, const vecchia_problem* probs, int n, int precision, 
                                              : default_tile(B.mixed, B.total_sites, std::max(B.max_S[b], 2), b);
         max_groups = std::max(max_groups, B.tiles[b].groups);
     }
-    B.fb_cap = B.mixed ? B.total_sites * max_groups : 0;
+    B.fb_cap = B.mixed ? B.total_sites * max_groups + vk::genz_items_slack(vk::device_sm_count(c ? c->device : 0)) : 0;
     B.lat.assign(n, nullptr);
     for (int i = 0; i < n; ++i) {
         if (!B.ok[i]) continue;
@@ -580,7 +580,7 @@ cudaError_t enqueue(const Batch& B, char* A, char* H, cudaStream_t s, bool with_
         if (!B.bucket_sites[b]) continue;
         e = vk::launch_genz(b, B.mixed, B.tiles[b], probs_d, (const int*)(blob_dev + B.b_segp[b]),
                             (const int2*)(blob_dev + B.b_segb[b]), B.bucket_segs[b], (int)B.bucket_sites[b],
-                            res_d, fbc, fbi, B.max_S[b], s);
+                            res_d, fbc, fbi, B.max_S[b], (int)B.fb_cap, s);
     }
     if (c && c->timing && e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
     if (B.mixed && e == cudaSuccess)
@@ -1672,7 +1672,9 @@ int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, i
                                          : default_tile(mixed, total_sites, std::max(max_S[b], 2), b);
         max_groups = std::max(max_groups, tiles[b].groups);
     }
-    const int64_t fb_cap = mixed ? std::max<int64_t>(total_sites * max_groups, 1) : 1;
+    const int64_t fb_cap =
+        mixed ? std::max<int64_t>(total_sites * max_groups + vk::genz_items_slack(vk::device_sm_count(c->device)), 1)
+              : 1;
     Carve dv(nullptr);
     const size_t o_delta = dv.off;
     dv.take<double>((size_t)shift_rows * kDim);
@@ -1742,7 +1744,7 @@ int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, i
         if (!bucket_sites[b]) continue;
         e = vk::launch_genz(b, mixed, tiles[b], probs_d, (const int*)(blob + b_segp[b]),
                             (const int2*)(blob + b_segb[b]), bucket_segs[b], (int)bucket_sites[b], nullptr,
-                            fbc, (int2*)(A + o_fbi), max_S[b], s);
+                            fbc, (int2*)(A + o_fbi), max_S[b], (int)fb_cap, s);
     }
     if (mixed && e == cudaSuccess)
         e = vk::launch_genz_fallback(max_bucket, probs_d, fbc, (int2*)(A + o_fbi), (int)fb_cap, nullptr, max_S_all, s);

@@ -506,6 +506,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 // `groups` shift groups (the group index varies fastest).  With an explicit
 // `items` list (the FP64 re-evaluation of flagged sites) an item is
 // (problem, site) with all shifts, and its count may live on the device.
+//
+// The last round of a launch: with items of equal size, a launch of n items
+// on a grid of G CTAs leaves n mod G CTAs with one item more than the rest,
+// and they finish alone at a fraction of their SMs' throughput.  So the sites
+// after `whole_sites` (those whose items would form that last round) are cut
+// into `tail_groups` shift groups instead of `groups`: more, smaller items
+// that spread over the whole grid.  A shift's partial means are computed by
+// one warp whatever the grouping, so the results do not change.
 struct ItemSrc {
     const int2* items;       // explicit (problem, site) items, or nullptr
     const int* dev_count;    // device-side count for `items`, or nullptr
@@ -514,16 +522,30 @@ struct ItemSrc {
     int n_segs;
     int n_items;
     int groups;              // shift groups per site (segment mode)
+    int whole_sites;         // sites [0, whole_sites) in `groups` groups, the rest in tail_groups
+    int tail_groups;
+    int fb_cap;              // capacity of the flagged-item list
 };
 
-__device__ __forceinline__ void item_of(const ItemSrc& src, int it, int2& ps, int& grp) {
+__device__ __forceinline__ void item_of(const ItemSrc& src, int it, int2& ps, int& grp, int& ngroups) {
     if (src.items) {
         ps = src.items[it];
         grp = 0;
+        ngroups = 1;
         return;
     }
-    const int site_item = it / src.groups;
-    grp = it - site_item * src.groups;
+    int site_item;
+    const int whole = src.whole_sites * src.groups;
+    if (it < whole) {
+        site_item = it / src.groups;
+        grp = it - site_item * src.groups;
+        ngroups = src.groups;
+    } else {
+        const int j = it - whole, k = j / src.tail_groups;
+        site_item = src.whole_sites + k;
+        grp = j - k * src.tail_groups;
+        ngroups = src.tail_groups;
+    }
     int lo = 0, hi = src.n_segs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -628,12 +650,11 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
     const int n_run = src.dev_count ? min(*src.dev_count, src.n_items) : src.n_items;
     for (int it = blockIdx.x; it < n_run; it += gridDim.x) {
         int2 item;
-        int grp;
-        item_of(src, it, item, grp);
+        int grp, groups;
+        item_of(src, it, item, grp, groups);
         const ProbDev& Pd = probs[item.x];
         const int64_t term = item.y;
         const int S = Pd.S;
-        const int groups = src.items ? 1 : src.groups;
         const int s_lo = (S * grp) / groups, s_hi = (S * (grp + 1)) / groups;
 
         // ---- prologue: block (warp 0), covariance (all warps), Cholesky (warp 0); FP64 ----
@@ -830,7 +851,7 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
                 R->status = (sm.bad == 1) ? VECCHIA_ERR_NOT_PD : VECCHIA_ERR_ARG;
             } else if (MODE == kModeFast && sm.flag && fallback_items) {
                 const int pos = atomicAdd(fallback_count, 1);
-                fallback_items[pos] = item;
+                if (pos < src.fb_cap) fallback_items[pos] = item;  // the callers size it for every item
             }
         }
         __syncthreads();
@@ -1051,9 +1072,24 @@ cudaError_t launch_one(const GenzTile& tile, const ProbDev* probs, const ItemSrc
         blocks_per_sm = it->second;
     }
     const int64_t cap = (int64_t)blocks_per_sm * device_sm_count(dev);
-    const int grid = (int)((src.n_items < cap) ? src.n_items : cap);
+    ItemSrc s2 = src;
+    if (!src.items && src.n_items > cap) {
+        // cut the sites of the last, partial round into more shift groups (as
+        // long as each piece keeps a shift per warp and the pieces fit one round)
+        const int g = src.groups, n_sites = src.n_items / g;
+        const int whole_sites = (int)(((int64_t)(src.n_items / cap) * cap) / g);
+        const int rest = n_sites - whole_sites;
+        int tg = g;
+        while (rest > 0 && 2 * tg * warps <= max_S && (int64_t)rest * 2 * tg <= cap) tg *= 2;
+        if (tg > g) {
+            s2.whole_sites = whole_sites;
+            s2.tail_groups = tg;
+            s2.n_items = whole_sites * g + rest * tg;
+        }
+    }
+    const int grid = (int)((s2.n_items < cap) ? s2.n_items : cap);
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, warps * 32, smem, st>>>(probs, src, tile.slices, max_S, results, fb_count, fb_items);
+    kern<<<grid, warps * 32, smem, st>>>(probs, s2, tile.slices, max_S, results, fb_count, fb_items);
     return cudaGetLastError();
 }
 
@@ -1062,7 +1098,7 @@ cudaError_t launch_one(const GenzTile& tile, const ProbDev* probs, const ItemSrc
 cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const ProbDev* probs,
                         const int* seg_prefix, const int2* seg_base, int n_segs, int n_sites,
                         ProbResult* results, int* fallback_count, int2* fallback_items, int max_S,
-                        cudaStream_t st) {
+                        int fb_capacity, cudaStream_t st) {
     if (n_sites <= 0) return cudaSuccess;
     GenzTile t = tile;
     if (t.slices < 1) t.slices = 1;
@@ -1070,7 +1106,8 @@ cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const Prob
     if (t.groups > max_S) t.groups = max_S;
     const int per_group = (max_S + t.groups - 1) / t.groups;
     while (t.slices > 1 && per_group * t.slices > kMaxUnits) --t.slices;
-    ItemSrc src{nullptr, nullptr, seg_prefix, seg_base, n_segs, n_sites * t.groups, t.groups};
+    ItemSrc src{nullptr, nullptr, seg_prefix, seg_base, n_segs, n_sites * t.groups, t.groups, n_sites, t.groups,
+                fb_capacity};
 #define VK_ARGS t, probs, src, max_S, results
 #define VK_CASE(IDX, DM)                                                                         \
     case IDX:                                                                                    \
@@ -1106,7 +1143,7 @@ cudaError_t launch_genz_fallback(int max_bucket, const ProbDev* probs, const int
                                  int max_S, cudaStream_t st) {
     if (capacity <= 0) return cudaSuccess;
     GenzTile t{4, 1, 1, 1};
-    ItemSrc src{fallback_items, fallback_count, nullptr, nullptr, 0, capacity, 1};
+    ItemSrc src{fallback_items, fallback_count, nullptr, nullptr, 0, capacity, 1, 0, 1, 0};
     if (max_bucket >= 7)  // blocks of more than 32 variables in the batch
         return launch_one<64, 1, kModeSafe>(t, probs, src, max_S, results, nullptr, nullptr, st);
     return launch_one<32, 1, kModeSafe>(t, probs, src, max_S, results, nullptr, nullptr, st);

@@ -139,7 +139,7 @@ extern "C" int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const doub
     const size_t o_delta = take(sizeof(double) * vk::kMaxS * kDim);
     const size_t o_dfix = take(sizeof(uint32_t) * vk::kMaxS * kDim);
     const size_t o_fbc = take(sizeof(int));
-    const size_t fb_cap = mixed ? (size_t)D * groups : 1;
+    const size_t fb_cap = mixed ? (size_t)D * groups + (size_t)vk::genz_items_slack(vk::device_sm_count(device)) : 1;
     const size_t o_fbi = take(sizeof(int2) * fb_cap);
     // parameter block, uploaded in one copy
     struct Params {
@@ -212,7 +212,7 @@ extern "C" int vecchia_log_cdf_noalloc(int device, void* cuda_stream, const doub
                               (uint32_t*)(base + o_dfix), st);
     if (e == cudaSuccess)
         e = vk::launch_genz(bucket, mixed, tile, &dpar->prob, dpar->seg_prefix, dpar->seg_base, 1, (int)D,
-                            &dpar->result, fbc, fbi, S, st);
+                            &dpar->result, fbc, fbi, S, (int)fb_cap, st);
     if (mixed && e == cudaSuccess)
         e = vk::launch_genz_fallback(bucket, &dpar->prob, fbc, fbi, (int)fb_cap, &dpar->result, S, st);
     if (e == cudaSuccess)

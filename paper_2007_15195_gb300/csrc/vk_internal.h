@@ -89,7 +89,11 @@ struct GenzTile {
 cudaError_t launch_genz(int bucket, bool mixed, const GenzTile& tile, const ProbDev* probs,
                         const int* seg_prefix, const int2* seg_base, int n_segs, int n_sites,
                         ProbResult* results, int* fallback_count, int2* fallback_items, int max_S,
-                        cudaStream_t st);
+                        int fb_capacity, cudaStream_t st);
+// Entries to add to a flagged-item list beyond (sites x shift groups): a launch
+// may cut its last round into smaller items, at most one grid's worth (of at
+// most 32 CTAs per SM) per bucket.
+inline int64_t genz_items_slack(int sm_count) { return (int64_t)kNumBuckets * 32 * sm_count; }
 // Log-space re-evaluation of the items the mixed kernel flagged (device-side
 // count), instantiated for the largest bucket of the batch.
 cudaError_t launch_genz_fallback(int max_bucket, const ProbDev* probs, const int* fallback_count,
