@@ -77,6 +77,9 @@ ALG_OPS_STEP = 34
 # the Genz kernel on the headline workload (m = 20, built-in tile:
 # genz_kernel<21, 2, fast>), from one ncu capture of that launch.
 GENZ_TRAFFIC_BYTES_M20 = 363_264
+# DRAM bytes of one launch of the FP64 Genz kernel on the headline workload
+# (genz_kernel<21, 1, FP64>), from one ncu capture of that launch.
+GENZ64_TRAFFIC_BYTES_M20 = 512_512
 # DRAM bytes of one launch of the full-Genz recursion kernel on the tensor
 # cores (full_genz_tc_kernel, 50x50 grid, D = 2,500, N = 4,096 x S = 16), from
 # one ncu capture of that launch: 13.26 GB read + 1.56 GB written.
@@ -458,7 +461,8 @@ def run_ours(args):
                     "p99_ms": float(np.percentile(ms64, 99)), "genz_kernel_ms": g64 * 1000.0}
         if w64 is not None:
             fp64_obj["roofline"] = {"bound": "alu", "achieved": w64 / g64 / 1e12, "peak": fp64_peak() / 1e12,
-                                    "unit": "TFLOP/s", "frac": w64 / g64 / fp64_peak(), "traffic": None,
+                                    "unit": "TFLOP/s", "frac": w64 / g64 / fp64_peak(),
+                                    "traffic": GENZ64_TRAFFIC_BYTES_M20 if m == 20 else None,
                                     "kernel": "genz_kernel (fp64)", "kernel_ms": g64 * 1000.0,
                                     "peak_source": "%d SMs x %d FP64 lanes x %.0f MHz (%s)"
                                                    % (SM_COUNT, FP64_LANES_PER_SM, SM_MAX_MHZ, PEAK_SOURCE),
@@ -479,6 +483,7 @@ def run_ours(args):
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": GENZ_TRAFFIC_BYTES_M20 if m == 20 else None,
                          "kernel": "genz_kernel (mixed)", "kernel_ms": genz_s * 1000.0,
+                         "lattice_steps_per_s": float(N) * S * float(np.sum(np.minimum(np.arange(D), m))) / genz_s,
                          "ops": "FP32-pipe lane operations, an FMA counting once; %d per Genz step "
                                 "+ q(q+1)/2 FMAs per point; peak = %d SMs x %d lanes x %.0f MHz"
                                 % (ALG_OPS_STEP, SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ),

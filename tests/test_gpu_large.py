@@ -89,3 +89,41 @@ def test_large_fp64_full_size(ctx, large_ordered):
     assert np.allclose(den[idx], oden, rtol=1e-10, atol=0), np.max(np.abs(den[idx] / oden - 1))
     mlp, _ = B.vecchia_log_cdf(ctx, ds, nbr, prob.m, prob.cov, du, prob.N, prob.S, 0, B.MIXED)
     assert abs(mlp - lp) <= mixed_tol(lp), (mlp, lp)
+
+
+def _last_variance_fraction(s, nbr, m, rho):
+    """Per term with m neighbours: L_qq^2 / Sigma_qq of its block under the
+    Matern 3/2 covariance (the last variable's conditional variance fraction;
+    near 0 when a neighbour nearly duplicates the site).  numpy Cholesky of
+    each block: only used to pick the worst-conditioned terms."""
+    D = s.shape[0]
+    idx = np.arange(m, D)
+    out = np.ones(D)
+    for c0 in range(0, idx.size, 8192):
+        ii = idx[c0:c0 + 8192]
+        blk = np.concatenate([nbr[ii, :m], ii[:, None]], axis=1)
+        p = s[blk]
+        r = np.sqrt(((p[:, :, None, :] - p[:, None, :, :]) ** 2).sum(-1)) * np.sqrt(3.0) / rho
+        L = np.linalg.cholesky((1.0 + r) * np.exp(-r))
+        out[ii] = L[:, -1, -1] ** 2
+    return out
+
+
+def test_large_mixed_on_the_worst_conditioned_terms(ctx, large_ordered):
+    """Near-duplicate sites make a term's block nearly singular; the mixed
+    path's FP64 factor and FP32 integrand must still meet the per-term bound
+    on the 24 worst-conditioned terms of the D = 100,000 problem."""
+    import torch
+    prob, s, u = large_ordered
+    ds, du = torch.from_numpy(s).cuda(), torch.from_numpy(u).cuda()
+    nbr = B.vecchia_neighbors(ctx, ds, prob.m)
+    nb_h = nbr.cpu().numpy()
+    frac = _last_variance_fraction(s, nb_h, prob.m, prob.cov[2])
+    idx = np.sort(np.argsort(frac)[:24])
+    assert frac[idx].max() < 1e-4  # genuinely ill-conditioned blocks
+    lp, se, terms, num, den = B.vecchia_log_cdf_terms(ctx, ds, nbr, prob.m, prob.cov, du, prob.N, prob.S, 5,
+                                                      B.MIXED)
+    onum, oden = O.vecchia_partials(s, nb_h, prob.m, prob.cov, u, prob.N, prob.S, 5, idx=idx)
+    t_or = np.log(onum.mean(1)) - np.log(oden.mean(1))
+    err = np.abs(terms.cpu().numpy()[idx] - t_or)
+    assert np.max(err) <= mixed_tol(lp) / prob.D, (np.max(err), frac[idx])

@@ -328,6 +328,24 @@ def test_two_points_per_lane_equal_one(ctx, m, N):
     assert np.array_equal(np.asarray(out[1][4]), np.asarray(out[2][4]))
 
 
+def test_last_round_split_leaves_results_unchanged(ctx):
+    """2,500 terms on the grid outnumber the resident CTAs, so the launch cuts
+    the sites of its last, partial round into more shift groups; with one
+    shift per item (16 groups) nothing is cut.  A shift's partial means come
+    from one warp either way: both precisions agree bit for bit."""
+    prob = inputs.grid50(m=20, N=512, S=16)
+    _, s, u, nbr = oracle_prepare(prob)
+    for prec in (B.FP64, B.MIXED):
+        out = []
+        for groups in (1, 16):
+            B.vecchia_set_tile(ctx, prec, -1, 4, 1 if prec == B.FP64 else 2, 1, groups)
+            out.append(B.vecchia_log_cdf_terms(ctx, s, nbr, prob.m, prob.cov, u, prob.N, prob.S, 4, prec))
+        B.vecchia_reset_tiles(ctx)
+        assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+        assert np.array_equal(np.asarray(out[0][3]), np.asarray(out[1][3]))
+        assert np.array_equal(np.asarray(out[0][4]), np.asarray(out[1][4]))
+
+
 def test_mixed_underflow_falls_back_to_log_space(ctx):
     """Thresholds far below the mean: FP32 conditional probabilities underflow
     in the fast mixed form, whose lattice means then fall below 2^-40; those
