@@ -8,9 +8,8 @@
 //   2. Cholesky factor, blocked right-looking in FP64: a factor of each
 //      32 x 32 diagonal block, a row-wise forward substitution of the rows
 //      below it, and the trailing update.  Every entry receives its terms in
-//      ascending k with fma and the pivot last: the operations of the
-//      row-by-row definition in its order, except that the rows below a
-//      diagonal block multiply by the pivots' reciprocals (one rounding more);
+//      ascending k with fma and the pivot division last: the operations of
+//      the row-by-row definition in its order;
 //   3. the rows of L scaled by 1/L_vv (u likewise);
 //   4. Genz's recursion.  FP64 (here): CTA tiles of P = 128 lattice points, in
 //      panels of 32 variables: the panel's conditional means
@@ -101,19 +100,16 @@ __global__ void __launch_bounds__(128) chol_diag_kernel(double* __restrict__ A, 
 }
 
 // Rows r >= k0 + 32 of the block column: x L_kk^T = a by forward
-// substitution, one thread per row.  The 32 pivots' reciprocals are formed
-// once per CTA: each entry is its terms in ascending k with fma, times the
-// reciprocal of the pivot (one rounding more than the definition's division;
-// GB300's FP64 division is a sequence of about ten FP64 operations).
+// substitution, one thread per row.  Each entry divides by its pivot (the
+// row-by-row definition's operation: a reciprocal would save FP64 work but
+// change the factor's last bits, and with them which exactly singular
+// block is reported).
 __global__ void chol_trsm_kernel(double* __restrict__ A, int D, int k0) {
     __shared__ double Lk[kCholB][kCholB + 1];
-    __shared__ double rdiag[kCholB];
     for (int x = threadIdx.x; x < kCholB * kCholB; x += blockDim.x) {
         const int r = x / kCholB, c = x % kCholB;
         Lk[r][c] = (c <= r) ? A[(int64_t)(k0 + r) * D + k0 + c] : 0.0;
     }
-    __syncthreads();
-    if (threadIdx.x < kCholB) rdiag[threadIdx.x] = 1.0 / Lk[threadIdx.x][threadIdx.x];
     __syncthreads();
     const int r = k0 + kCholB + blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= D) return;
@@ -124,7 +120,7 @@ __global__ void chol_trsm_kernel(double* __restrict__ A, int D, int k0) {
         double acc = row[j];
 #pragma unroll
         for (int i = 0; i < j; ++i) acc = fma(-x[i], Lk[j][i], acc);
-        x[j] = acc * rdiag[j];
+        x[j] = acc / Lk[j][j];
     }
 #pragma unroll
     for (int j = 0; j < kCholB; ++j) row[j] = x[j];
