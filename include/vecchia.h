@@ -165,7 +165,11 @@ typedef struct {
     uint64_t seed;
     vecchia_cov cov;
     int32_t group;        /* 0: one term per site (Eq. vecchia-cdf); p: joint groups of p sites */
-    int32_t reserved;
+    int32_t cond_max;     /* group p: the largest number of conditioning sites in any row (its
+                           * leading non-negative entries), if known (0 = m).  Picks the kernel
+                           * instantiation (the block size cond_max + p rather than m + p);
+                           * a row with more entries makes its term fail with
+                           * VECCHIA_ERR_ARG.  vecchia_grouped_log_cdf computes it. */
 } vecchia_problem;
 
 /* Many independent problems in one set of launches (the terms of every
@@ -173,7 +177,8 @@ typedef struct {
  * across problems).  The arrays of all problems must be of one kind (all host
  * or all device).  log_p, std_err, status are host arrays of n_probs; a
  * problem that fails gets its own status and NaN results; the call returns
- * VECCHIA_OK when the batch ran, even if some problems failed. */
+ * VECCHIA_OK when the batch ran, even if some problems failed (a batch of
+ * one problem returns that problem's status). */
 int vecchia_log_cdf_batch(vecchia_ctx* ctx, const vecchia_problem* probs, int n_probs,
                           int precision, double* log_p, double* std_err, int32_t* status);
 
@@ -208,7 +213,9 @@ int vecchia_group_conditioning(vecchia_ctx* ctx, const double* sites_ordered, in
  * (ceil(D/p) x cmax, from vecchia_group_conditioning or the caller: rows
  * ascending, entries < k p, -1 padded after the last).  Terms have up to
  * cmax + p <= VECCHIA_MAX_M + 1 variables.  On VECCHIA_ERR_NOT_PD or a bad
- * row, vecchia_last_error_site() gives the group index. */
+ * row, vecchia_last_error_site() gives the group index.  The call first finds
+ * the longest row (a reduction on the device when cond is device memory) and
+ * evaluates with the kernel sized for it (vecchia_problem.cond_max). */
 int vecchia_grouped_log_cdf(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, int p,
                             const int32_t* cond, int cmax, vecchia_cov cov, const double* u, int64_t N,
                             int S, uint64_t seed, int precision, double* log_p, double* std_err);

@@ -49,7 +49,7 @@ class vecchia_cov(C.Structure):
 class vecchia_problem(C.Structure):
     _fields_ = [("sites", C.c_void_p), ("nbr", C.c_void_p), ("u", C.c_void_p), ("D", C.c_int64),
                 ("m", C.c_int32), ("S", C.c_int32), ("N", C.c_int64), ("seed", C.c_uint64),
-                ("cov", vecchia_cov), ("group", C.c_int32), ("reserved", C.c_int32)]
+                ("cov", vecchia_cov), ("group", C.c_int32), ("cond_max", C.c_int32)]
 
 
 class vecchia_segment(C.Structure):
@@ -408,13 +408,15 @@ def _problem_array(problems):
         nb = _i32(p["nbr"]) if m > 0 else None
         keep.append((s, uu, nb))
         arr[i] = vecchia_problem(_ptr(s), _ptr(nb), _ptr(uu), s.shape[0], m, int(p["S"]), int(p["N"]),
-                                 int(p.get("seed", 0)), make_cov(p["cov"]), int(p.get("group", 0)), 0)
+                                 int(p.get("seed", 0)), make_cov(p["cov"]), int(p.get("group", 0)),
+                                 int(p.get("cond_max", 0)))
     return arr, keep
 
 
 def vecchia_log_cdf_batch(ctx, problems, precision=MIXED):
-    """problems: list of dicts with keys sites, nbr, m, cov, u, N, S, seed (arrays all
-    host or all device).  Returns numpy arrays (log_p, std_err, status)."""
+    """problems: list of dicts with keys sites, nbr, m, cov, u, N, S, seed and
+    optionally group, cond_max (arrays all host or all device).  Returns numpy
+    arrays (log_p, std_err, status)."""
     n = len(problems)
     arr, keep = _problem_array(problems)
     lp = np.empty(n)

@@ -38,6 +38,7 @@ struct vecchia_ctx {
     // test switch that makes its copy lane issue nothing
     uint64_t full_wait_ns = 0;
     int full_withhold = 0;
+    int* small_dev = nullptr;  // a device int for small reductions (allocated on first use)
 };
 
 namespace vk {
@@ -271,7 +272,7 @@ void set_cov(ProbDev& d, const vecchia_cov& c) {
 
 int check_problem(const vecchia_problem& p) {
     if (p.D < 1 || p.D > INT_MAX / 2 || !p.sites || !p.u) return VECCHIA_ERR_ARG;
-    if (p.m < 0 || p.group < 0) return VECCHIA_ERR_ARG;
+    if (p.m < 0 || p.group < 0 || p.cond_max < 0 || p.cond_max > p.m) return VECCHIA_ERR_ARG;
     if (p.m > VECCHIA_MAX_M || vk::max_term_dim(p.m, p.group) > VECCHIA_MAX_M + 1)
         return VECCHIA_ERR_UNSUPPORTED;
     if (p.m > 0 && !p.nbr) return VECCHIA_ERR_ARG;
@@ -397,7 +398,7 @@ int prepare(vecchia_ctx* c, const vecchia_problem* probs, int n, int precision, 
     B.bucket_of.assign(n, -1);
     for (int i = 0; i < n; ++i) {
         if (!B.ok[i]) continue;
-        const int b = vk::bucket_of(vk::max_term_dim(probs[i].m, probs[i].group));
+        const int b = vk::bucket_of(vk::max_term_dim(probs[i].m, probs[i].group, probs[i].cond_max));
         const int64_t T = vk::n_terms_of(probs[i].D, probs[i].group);
         B.bucket_of[i] = b;
         B.bucket_sites[b] += T;
@@ -937,6 +938,7 @@ int vecchia_destroy(vecchia_ctx* c) {
     cudaStreamSynchronize(c->stream);
     if (c->arena) cudaFree(c->arena);
     if (c->aux) cudaFree(c->aux);
+    if (c->small_dev) cudaFree(c->small_dev);
     if (c->host_stage) cudaFreeHost(c->host_stage);
     for (auto& kv : c->lattice_dev) cudaFree(kv.second);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1269,6 +1271,32 @@ int vecchia_grouped_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, int 
     pr.seed = seed;
     pr.cov = cov;
     pr.group = p;
+    // the largest conditioning set present picks the kernel instantiation
+    // (rows are often much shorter than their width cmax)
+    if (c && cond && cmax > 0 && D >= 1) {
+        const int64_t G = (D + p - 1) / p;
+        int cm = 0;
+        if (is_device_ptr(cond)) {
+            if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+            cudaError_t e = cudaSuccess;
+            if (!c->small_dev) e = cudaMalloc(&c->small_dev, 256);
+            if (e == cudaSuccess) e = vk::launch_rows_max(cond, G, cmax, c->small_dev, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&cm, c->small_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return VECCHIA_ERR_CUDA;
+            }
+        } else {
+            for (int64_t k = 0; k < G; ++k) {
+                const int32_t* row = cond + k * (int64_t)cmax;
+                int n = 0;
+                while (n < cmax && row[n] >= 0) ++n;
+                cm = std::max(cm, n);
+            }
+        }
+        pr.cond_max = cm;
+    }
     int32_t status = VECCHIA_OK;
     return run_problems(c, &pr, 1, precision, log_p, std_err, &status, nullptr, nullptr, nullptr);
 }
@@ -1654,7 +1682,7 @@ int vecchia_partials_async(vecchia_ctx* c, const vecchia_segment* segs, int n, i
     std::vector<uint32_t*> lat(n);
     for (int i = 0; i < n; ++i) {
         const auto& p = segs[i].prob;
-        bk[i] = vk::bucket_of(vk::max_term_dim(p.m, p.group));
+        bk[i] = vk::bucket_of(vk::max_term_dim(p.m, p.group, p.cond_max));
         max_S_all = std::max(max_S_all, p.S);
         max_bucket = std::max(max_bucket, bk[i]);
         shift_rows += p.S;

@@ -879,6 +879,23 @@ cudaError_t launch_group_union(const int32_t* per_site, int64_t D, int m, int p,
     return cudaGetLastError();
 }
 
+// The largest number of leading non-negative entries over G rows of width m.
+__global__ void rows_max_kernel(const int32_t* __restrict__ rows, int64_t G, int m, int* __restrict__ out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G) return;
+    const int32_t* row = rows + k * (int64_t)m;
+    int c = 0;
+    while (c < m && row[c] >= 0) ++c;
+    atomicMax(out, c);
+}
+
+cudaError_t launch_rows_max(const int32_t* rows, int64_t G, int m, int* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), st);
+    if (e != cudaSuccess || G <= 0 || m <= 0) return e;
+    rows_max_kernel<<<(int)((G + 255) / 256), 256, 0, st>>>(rows, G, m, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_group_random(int64_t D, int p, int kk, uint64_t seed, int cmax, int32_t* cond,
                                 int32_t* count, cudaStream_t st) {
     const int64_t G = (D + p - 1) / p;

@@ -32,6 +32,10 @@ inline int bucket_of(int d) {
 
 // Largest term dimension of a problem: m + 1 (classic), m + p (groups of p).
 inline int max_term_dim(int m, int group) { return group > 0 ? m + group : m + 1; }
+// The same for a problem whose group rows hold at most cond_max sites (0: m).
+inline int max_term_dim(int m, int group, int cond_max) {
+    return max_term_dim((group > 0 && cond_max > 0 && cond_max < m) ? cond_max : m, group);
+}
 // Number of Vecchia terms: one per site (classic) or per group of p sites.
 inline int64_t n_terms_of(int64_t D, int group) { return group > 0 ? (D + group - 1) / group : D; }
 
@@ -133,6 +137,8 @@ cudaError_t launch_group_union(const int32_t* per_site, int64_t D, int m, int p,
                                int32_t* count, int* overflow, cudaStream_t st);
 // Random conditioning rows: a uniform subset of min(kk, k p) sites before
 // group k (Floyd's algorithm on Philox4x32-10 draws), ascending.
+// *out = the largest number of leading non-negative entries over G rows of width m.
+cudaError_t launch_rows_max(const int32_t* rows, int64_t G, int m, int* out, cudaStream_t st);
 cudaError_t launch_group_random(int64_t D, int p, int kk, uint64_t seed, int cmax, int32_t* cond,
                                 int32_t* count, cudaStream_t st);
 

@@ -290,3 +290,27 @@ def test_unordered_call_equals_the_four_calls(ctx, order, D, m, device):
     assert got == ref
     p_ref = perm.cpu().numpy() if device else perm
     assert np.array_equal(got_perm, p_ref)
+
+
+def test_grouped_block_size_from_the_longest_row(ctx):
+    """Grouped rows are often far shorter than their width: the grouped call
+    sizes its kernel by the longest row (cond_max), and a batch with the
+    hint equals one without it bit for bit; a hint shorter than a row makes
+    that group fail with VECCHIA_ERR_ARG."""
+    import torch
+    prob = inputs.grid50(m=5, N=512, S=4)  # on the grid in xy order the members' neighbours overlap
+    perm = O.order(prob.sites, O.ORDER_XY)
+    s = torch.from_numpy(np.ascontiguousarray(prob.sites[perm])).cuda()
+    u = torch.from_numpy(np.ascontiguousarray(prob.u[perm])).cuda()
+    p, m = 5, 5
+    cond, cnt = B.vecchia_group_conditioning(ctx, s, p, m, B.COND_NEAREST, seed=1, cmax=p * m)
+    cmax_used = int(cnt.max().item())
+    assert 1 + p < cmax_used + p <= 21 < p * m + p  # a smaller kernel than the row width asks for
+    for prec in (B.FP64, B.MIXED):
+        lp, se = B.vecchia_grouped_log_cdf(ctx, s, p, cond, prob.cov, u, prob.N, prob.S, seed=3, precision=prec)
+        item = dict(sites=s, nbr=cond, m=p * m, cov=prob.cov, u=u, N=prob.N, S=prob.S, seed=3, group=p)
+        ref = B.vecchia_log_cdf_batch(ctx, [item], prec)             # bucket from the row width
+        hint = B.vecchia_log_cdf_batch(ctx, [dict(item, cond_max=cmax_used)], prec)
+        assert (lp, se) == (ref[0][0], ref[1][0]) == (hint[0][0], hint[1][0])
+        short = B.vecchia_log_cdf_batch(ctx, [dict(item, cond_max=1), item], prec)  # a 9-variable kernel
+        assert short[2][0] == B.ERR_ARG and short[2][1] == B.OK and short[0][1] == lp
