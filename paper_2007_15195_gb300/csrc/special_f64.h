@@ -7,8 +7,8 @@
 //
 //   Phi(-a), a >= 0:  T = exp(-a^2/2) R(a), R(a) = erfcx(a/sqrt 2)/2 a
 //     piecewise degree-9 polynomial (intervals of width 1/4), the exponential
-//     table-driven (2^(j/256), two-constant reduction, Taylor to r^4), a^2/2
-//     carried as an exact sum hi + lo; about 25 FP64 operations, relative
+//     table-driven (2^(j/256), two-constant reduction, Taylor to r^4), a^2
+//     carried as an exact sum hi + lo; about 24 FP64 operations, relative
 //     error ~1e-15 (tables and method: special_f64.cuh, fit_special64.py).
 //   Phi^{-1}(s), s = min(p, q): a first guess a0 from the FP32 quantile of
 //     the mixed path (evaluated from log2 p + log2 q, taken from the doubles'
@@ -55,10 +55,20 @@ __device__ __forceinline__ double rcp_approx(double x) {
 // 2^n as a double for -1022 <= n <= 1023 (integer instructions only).
 __device__ __forceinline__ double pow2i(int n) { return __hiloint2double((n + 1023) << 20, 0); }
 
+// Comparisons of non-negative doubles as integers: for x, y >= +0 (and NaN
+// above +inf) the bit patterns order as the values, so these take the integer
+// pipe instead of GB300's 1/64-rate FP64 pipe.
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double max_nonneg(double x, double y) {
+    return __longlong_as_double(max(bits(x), bits(y)));
+}
+__device__ __forceinline__ double abs_bits(double x) { return __longlong_as_double(bits(x) & 0x7fffffffffffffffll); }
+__device__ __forceinline__ bool sign_bit(double x) { return bits(x) < 0; }
+
 // T = Phi(-a) for a >= 0, and (WANT_PHI) phi(a) = exp(-a^2/2)/sqrt(2 pi).
 template <bool WANT_PHI>
 __device__ __forceinline__ double tail(const Tables64& tb, double a, double& phi) {
-    if (!(a < 38.75)) {  // Phi(-a) below the smallest double (and a = inf or NaN)
+    if (bits(a) >= 0x4043600000000000ll) {  // a >= 38.75 (and inf, NaN): Phi(-a) below the smallest double
         if constexpr (WANT_PHI) phi = 0.0;
         return 0.0;
     }
@@ -71,19 +81,20 @@ __device__ __forceinline__ double tail(const Tables64& tb, double a, double& phi
     double Rv = c[kRDeg];
 #pragma unroll
     for (int k = kRDeg - 1; k >= 0; --k) Rv = fma(Rv, d, c[k]);
-    // a^2/2 = hi + lo exactly
-    const double ha = 0.5 * a;
-    const double hi = a * ha;
-    const double lo = fma(a, ha, -hi);
-    // exp(-hi - lo): k = round(-hi 256/ln2), r = -hi - k ln2/256 - lo
-    const double tk = fma(-hi, kExpInv, kMagic);
+    // a^2 = hi + lo exactly
+    const double hi = a * a;
+    const double lo = fma(a, a, -hi);
+    // exp(-(hi + lo)/2): k = round(-hi 128/ln2), s = -hi - k ln2/128 - lo = 2 r
+    // with |r| <= ln2/512; exp(r) = exp(s/2) by its Taylor polynomial in s
+    // (every step scaled by 2, so no halving of a^2 is needed)
+    const double tk = fma(-hi, 0.5 * kExpInv, kMagic);
     const int k = __double2loint(tk);
     const double kd = tk - kMagic;
-    double r = fma(kd, -kExpHi, -hi);
-    r = fma(kd, -kExpLo, r);
-    r = r - lo;
-    double p = fma(fma(fma(r, 1.0 / 24.0, 1.0 / 6.0), r, 0.5), r, 1.0);
-    p = fma(p, r, 1.0);
+    double r2 = fma(kd, -2.0 * kExpHi, -hi);
+    r2 = fma(kd, -2.0 * kExpLo, r2);
+    r2 = r2 - lo;
+    double p = fma(fma(fma(r2, 1.0 / 384.0, 1.0 / 48.0), r2, 0.125), r2, 0.5);
+    p = fma(p, r2, 1.0);
     const double e = tb.E[k & ((1 << kExpBits) - 1)] * p;  // 2^(j/256) exp(r)
     const int n = k >> kExpBits;                            // -1070 < n <= 0
     double T;
@@ -102,10 +113,11 @@ __device__ __forceinline__ double tail(const Tables64& tb, double a, double& phi
 // Phi(z) and 1 - Phi(z), the smaller one from the tail to full precision.
 __device__ __forceinline__ void phi_pair(const Tables64& tb, double z, double& e, double& ec) {
     double unused;
-    const double t = tail<false>(tb, fabs(z), unused);
+    const double t = tail<false>(tb, abs_bits(z), unused);
     const double u = 1.0 - t;
-    e = (z < 0.0) ? t : u;
-    ec = (z < 0.0) ? u : t;
+    const bool neg = sign_bit(z);  // -0 takes the first branch: t = u = 1/2 there
+    e = neg ? t : u;
+    ec = neg ? u : t;
 }
 
 // log2 of a positive normal double as an FP32 value (exponent and the top 20
@@ -137,8 +149,8 @@ __device__ __forceinline__ double to_f64_pos(float f) {
 // 2^-1000 (as the definition's quantile).
 __device__ __forceinline__ double phiinv_pq(const Tables64& tb, double p, double q) {
     const double lo = 9.3326361850321887899e-302;  // 2^-1000
-    const double pc = fmax(p, lo), qc = fmax(q, lo);
-    const bool lower = pc <= qc;
+    const double pc = max_nonneg(p, lo), qc = max_nonneg(q, lo);  // p, q >= 0
+    const bool lower = bits(pc) <= bits(qc);
     const double s = lower ? pc : qc;
     const double o = lower ? qc : pc;
     // first guess: the FP32 quantile's magnitude from L = log2(s o)
@@ -150,6 +162,7 @@ __device__ __forceinline__ double phiinv_pq(const Tables64& tb, double p, double
         f = special::finv_tail(__fmul_rn(-special::kLn2, __fadd_rn(L, 2.0f)));
     const float a0f = fmaxf(__fmul_rn(__fsub_rn(to_f32_unit(o), to_f32_unit(s)), f), 0.0f);
     const double a0 = to_f64_pos(a0f);
+    const double ha0 = to_f64_pos(__fmul_rn(a0f, 0.5f));  // a0 / 2 exactly
     // one Halley step on T(a) = s
     double phi;
     const double T = tail<true>(tb, a0, phi);
@@ -157,8 +170,8 @@ __device__ __forceinline__ double phiinv_pq(const Tables64& tb, double p, double
     const double rinv = rcp_approx(phi);
     double d = num * rinv;
     d = fma(fma(-phi, d, num), rinv, d);
-    const double a1 = fma(d, fma(0.5 * a0, d, 1.0), a0);
-    return lower ? -a1 : a1;
+    const double a1 = fma(d, fma(ha0, d, 1.0), a0);
+    return __longlong_as_double(bits(a1) ^ (lower ? (long long)0x8000000000000000ull : 0ll));  // -a1 below 1/2
 }
 
 }  // namespace special64
