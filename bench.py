@@ -194,15 +194,16 @@ def alu_roofline(work_ops, seconds, kernel, note=None):
 
 # FP64-pipe roofline of the FP64 Genz kernel: FP64 operations per Genz step of
 # the formulation the kernel evaluates (an FMA counting once) -- running
-# product 1, lattice-weighted probabilities 2, Phi^{-1} 33 (Phi(-a0) and
-# phi(a0) at the first guess 27: interval map 2, degree-9 polynomial 9, a^2
-# as hi + lo 2, exponential 10, products 4; residual, quotient with one
-# correction and Halley factor 6), standardisation 1, Phi 26 (Phi(-|z|) 25,
+# product 1, lattice-weighted probabilities 2, Phi^{-1} 30 (Phi(-a0) and
+# phi(a0) at the first guess 24: interval map 2, degree-8 polynomial 8, a^2
+# as hi + lo 2, exponential 10, products 2; residual, quotient with one
+# correction and Halley factor 6), standardisation 1, Phi 24 (Phi(-|z|) 23,
 # 1 - T 1) -- plus (t + 1) FMAs for the conditional mean of row t + 1.
-# Compares, min/max, selects and the integer lattice and exponent work are
-# not counted (the kernel does them with integer instructions).
-FP64_OPS_STEP = 63
-FP64_OPS_NOTE = ("FP64-pipe lane operations, an FMA counting once; 63 per Genz step + q(q+1)/2 FMAs per "
+# Compares, min/max, selects, powers of two and the integer lattice and
+# exponent work are not counted (the kernel does them with integer
+# instructions).
+FP64_OPS_STEP = 58
+FP64_OPS_NOTE = ("FP64-pipe lane operations, an FMA counting once; 58 per Genz step + q(q+1)/2 FMAs per "
                  "point; peak = SMs x 2 FP64 lanes x max SM clock")
 
 

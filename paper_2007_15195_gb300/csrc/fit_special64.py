@@ -7,8 +7,8 @@ Writes special_f64.cuh next to this script.  The form: for a >= 0,
 with R (smooth and slowly varying: 1/2 at 0, ~ 1/(a sqrt(2 pi)) for large a)
 a piecewise polynomial and the Gaussian factor a table-driven exponential:
 
-  * R on the intervals centred at a_i = i/4, |a - a_i| <= 1/8, i = 0..154
-    (a <= 38.625, where Phi(-a) is below the smallest double): a degree-9
+  * R on the intervals centred at a_i = i/8, |a - a_i| <= 1/16, i = 0..310
+    (a < 38.75; beyond, Phi(-a) is below the smallest double): a degree-8
     polynomial in d = a - a_i per interval, fitted in the Chebyshev sense by
     mpmath (chebyfit) against R evaluated at 40 digits, rounded to doubles;
   * exp(x), x = -a^2/2 <= 0: k = round(x 256 / ln 2), r = x - k ln2/256 by
@@ -31,9 +31,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "special_f64.cuh")
 mp.mp.dps = 40
 
-H = 0.25          # interval width in a
-NINT = 155        # centres 0, 1/4, ..., 38.5
-DEG = 9
+H = 0.125         # interval width in a
+NINT = 311        # centres 0, 1/8, ..., 38.75
+DEG = 8
 EXP_BITS = 8      # 2^(j/256) table
 
 
@@ -87,7 +87,7 @@ def emit(rows, hi, lo, inv, table, worst_exact, worst_f64):
         "namespace vk {",
         "namespace special64 {",
         "",
-        "// R(a) on |a - i/4| <= 1/8: sum_k kR[i][k] d^k, d = a + kR[i][%d]; worst relative" % (DEG + 1),
+        "// R(a) on |a - i h| <= h/2, h = %g: sum_k kR[i][k] d^k, d = a + kR[i][%d]; worst relative" % (H, DEG + 1),
         "// error %.2e (exact arithmetic), %.2e (double, no fma)" % (worst_exact, worst_f64),
         "constexpr int kRIntervals = %d, kRDeg = %d, kRStride = %d;" % (NINT, DEG, DEG + 3),
         "constexpr double kRScale = %s;  // 1 / width" % fmt(1.0 / H),

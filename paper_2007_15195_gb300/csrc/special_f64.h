@@ -6,9 +6,9 @@
 // integer and FP32 instructions:
 //
 //   Phi(-a), a >= 0:  T = exp(-a^2/2) R(a), R(a) = erfcx(a/sqrt 2)/2 a
-//     piecewise degree-9 polynomial (intervals of width 1/4), the exponential
+//     piecewise degree-8 polynomial (intervals of width 1/8), the exponential
 //     table-driven (2^(j/256), two-constant reduction, Taylor to r^4), a^2
-//     carried as an exact sum hi + lo; about 24 FP64 operations, relative
+//     carried as an exact sum hi + lo; about 23 FP64 operations, relative
 //     error ~1e-15 (tables and method: special_f64.cuh, fit_special64.py).
 //   Phi^{-1}(s), s = min(p, q): a first guess a0 from the FP32 quantile of
 //     the mixed path (evaluated from log2 p + log2 q, taken from the doubles'
@@ -72,7 +72,7 @@ __device__ __forceinline__ double tail(const Tables64& tb, double a, double& phi
         if constexpr (WANT_PHI) phi = 0.0;
         return 0.0;
     }
-    // R(a) on the interval whose centre i/4 is nearest to a
+    // R(a) on the interval whose centre i/8 is nearest to a
     const double ti = fma(a, kRScale, kMagic);
     int i = __double2loint(ti);
     i = min(max(i, 0), kRIntervals - 1);
@@ -95,16 +95,19 @@ __device__ __forceinline__ double tail(const Tables64& tb, double a, double& phi
     r2 = r2 - lo;
     double p = fma(fma(fma(r2, 1.0 / 384.0, 1.0 / 48.0), r2, 0.125), r2, 0.5);
     p = fma(p, r2, 1.0);
-    const double e = tb.E[k & ((1 << kExpBits) - 1)] * p;  // 2^(j/256) exp(r)
-    const int n = k >> kExpBits;                            // -1070 < n <= 0
+    const double e = tb.E[k & ((1 << kExpBits) - 1)] * p;  // 2^(j/256) exp(r), in [1, 2)
+    const int n = k >> kExpBits;                            // -1084 < n <= 0
+    const double v = e * Rv;                                // R(a) >= 0.0103: v in [2^-7, 2)
     double T;
-    if (n >= -1021) {
-        const double s = pow2i(n);
-        T = (e * Rv) * s;
-        if constexpr (WANT_PHI) phi = (e * kSqrt2PiInv) * s;
-    } else {  // below the normal range: two exact scalings
-        const double s1 = pow2i(-1021), s2 = pow2i(n + 1021);
-        T = ((e * Rv) * s1) * s2;
+    if (n >= -1000) {  // v 2^n stays normal: add n to the exponent field
+        T = __hiloint2double(__double2hiint(v) + (n << 20), __double2loint(v));
+        if constexpr (WANT_PHI) {
+            const double w = e * kSqrt2PiInv;
+            phi = __hiloint2double(__double2hiint(w) + (n << 20), __double2loint(w));
+        }
+    } else {  // near or below the normal range: two exact scalings
+        const double s1 = pow2i(-1000), s2 = pow2i(n + 1000);
+        T = (v * s1) * s2;
         if constexpr (WANT_PHI) phi = ((e * kSqrt2PiInv) * s1) * s2;
     }
     return T;
