@@ -79,7 +79,7 @@ ALG_OPS_STEP = 34
 GENZ_TRAFFIC_BYTES_M20 = 363_264
 # DRAM bytes of one launch of the FP64 Genz kernel on the headline workload
 # (genz_kernel<21, 1, FP64>), from one ncu capture of that launch.
-GENZ64_TRAFFIC_BYTES_M20 = 512_512
+GENZ64_TRAFFIC_BYTES_M20 = 497_408
 # DRAM bytes of one launch of the full-Genz recursion kernel on the tensor
 # cores (full_genz_tc_kernel, 50x50 grid, D = 2,500, N = 4,096 x S = 16), from
 # one ncu capture of that launch: 13.26 GB read + 1.56 GB written.
