@@ -57,11 +57,12 @@ def workload_for(m):
 #          an FMA counting as one operation).
 #   algorithmic work per Genz step (one lattice coordinate of one point):
 #          ALG_OPS_STEP FP32 operations of the formulation the kernel evaluates
-#          -- lattice coordinate and tent map 5 (scale, 1-w, w e, q, product),
-#          Phi^{-1} 14 (p q, map of log2(p q), 10-term polynomial, p - q, scale),
-#          Phi 15 (1 + |z| k, map of t, 9-term polynomial, |z| c, exponent,
-#          t 2^a, 1 - tail) -- plus (t + 1) FMAs for the conditional mean of
-#          row t + 1, i.e. q(q+1)/2 FMAs per point of a q-neighbour term.
+#          -- lattice coordinate and tent map 5 (scale, 16 - 16w, 16 w e,
+#          16 q, running product), Phi^{-1} 13 (p q, 10 fma of the polynomial
+#          in log2(256 p q) itself, p - q, scale), Phi 14 (1 + |zs| k, map of
+#          t, 9-term polynomial, exponent -zs^2 + P as one fma, t 2^a,
+#          1 - tail) -- plus (t + 1) FMAs for the conditional mean of row
+#          t + 1, i.e. q(q+1)/2 FMAs per point of a q-neighbour term.
 #          Selects, min/max, integer and special-function-unit instructions
 #          are not counted.
 SM_COUNT = 152          # replaced by the device's SM count (init_peaks)
@@ -72,11 +73,11 @@ PEAK_SOURCE = "GB300 nominal: 152 SMs, 2070 MHz"
 # FP32 rate (1.25 TFLOP/s FP64 nominal = 152 SMs x 2 FMA lanes x 2 flops x
 # 2.07 GHz).
 FP64_LANES_PER_SM = 2
-ALG_OPS_STEP = 34
+ALG_OPS_STEP = 32
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the Genz kernel on the headline workload (m = 20, built-in tile:
 # genz_kernel<21, 2, fast>), from one ncu capture of that launch.
-GENZ_TRAFFIC_BYTES_M20 = 363_264
+GENZ_TRAFFIC_BYTES_M20 = None
 # DRAM bytes of one launch of the FP64 Genz kernel on the headline workload
 # (genz_kernel<21, 1, FP64>), from one ncu capture of that launch.
 GENZ64_TRAFFIC_BYTES_M20 = 497_408

@@ -393,8 +393,10 @@ int vecchia_set_full_genz_wait(vecchia_ctx* ctx, uint64_t limit_ns, int withhold
 /* Diagnostic: the FP32 special functions of the mixed path on n values (x and
  * out device arrays of float): which = 0: Phi(x); 1: 1 - Phi(x); 2: log2 Phi(x)
  * for x < -9 (NaN otherwise); 3: Phi^{-1}(x), x in (0, 1); 4: Phi^{-1}(2^x) for
- * x < -64.  These are the maps of Genz's separation of variables (Sec. 2.2)
- * in the precision the mixed path evaluates them. */
+ * x < -64; the forms of the fast mixed step: 5: Phi(x / k) and 6: 1 - Phi(x / k),
+ * k = sqrt(log2(e) / 2) (its recursion carries k z); 7: Phi^{-1}(x) from 16 x
+ * and 16 (1 - x).  These are the maps of Genz's separation of variables
+ * (Sec. 2.2) in the precision the mixed path evaluates them. */
 int vecchia_eval_special(vecchia_ctx* ctx, int which, const float* x, int64_t n, float* out);
 
 /* Diagnostic: the FP64 special functions of the FP64 path on n values (x and

@@ -1937,7 +1937,7 @@ int vecchia_reset_tiles(vecchia_ctx* c) {
 }
 
 int vecchia_eval_special(vecchia_ctx* c, int which, const float* x, int64_t n, float* out) {
-    if (!c || which < 0 || which > 4 || n < 0 || (n > 0 && (!x || !out))) return VECCHIA_ERR_ARG;
+    if (!c || which < 0 || which > 7 || n < 0 || (n > 0 && (!x || !out))) return VECCHIA_ERR_ARG;
     if (n == 0) return VECCHIA_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
     if (!is_device_ptr(x) || !is_device_ptr(out)) return VECCHIA_ERR_ARG;

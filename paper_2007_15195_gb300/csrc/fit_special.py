@@ -108,6 +108,28 @@ def fit_inv(name, lo, hi, var, deg):
                 f32_err=err32, note="sqrt(2) erfinv(y)/y on %s in [%g, %g]" % (var, xlo, xhi))
 
 
+def fit_inv1_scaled(deg=10):
+    """The central quantile piece for callers that carry 16 p and 16 q.
+
+    With pk = 16 p and qk = 16 q (exact power-of-two scalings of p and q),
+    L' = log2(pk qk) = log2(r (1 - r)) + 8 and w = -ln 2 (L' - 6).  Fitted on
+    w in [0, 12 ln 2], the map to [-1, 1] is u = -L'/6 with no offset, so the
+    polynomial is re-expressed in L' itself (coefficients c_k (-1/6)^k) and
+    divided by 16: Phi^{-1}(p) = (pk - qk) f16(L') needs no map of L'."""
+    hi = 12.0 * np.log(2.0)
+    p = fit_inv("INV1S", 0.0, hi, "w", deg)
+    k = np.arange(len(p["coef"]))
+    coef = p["coef"] * (-1.0 / 6.0) ** k / 16.0
+    w = np.linspace(0.0, hi, 200001)
+    w[0] = 1e-14
+    Lp = (6.0 - w / np.log(2.0)).astype(np.float32).astype(np.float64)
+    got = horner_f32(coef, Lp)
+    f = finv_target(w) * np.sqrt(2.0) / 16.0
+    err32 = float(np.max(np.abs(got - f) / np.abs(f)))
+    return dict(name="INV1S", a=1.0, b=0.0, coef=coef, fit_err=p["fit_err"], f32_err=err32,
+                note="sqrt(2) erfinv(y)/y / 16 as a polynomial in L' = log2(256 r (1-r)), w in [0, %g]" % hi)
+
+
 def emit(pieces):
     lines = [
         "// special_f32.cuh -- generated by fit_special.py; do not edit by hand.",
@@ -130,6 +152,9 @@ def emit(pieces):
     lines.append("constexpr float kINV1LA = %.9ef, kINV1LB = %.9ef, kINV1Lmin = %.9ef;" % (
         -inv1["a"] * ln2, inv1["b"] - 2.0 * inv1["a"] * ln2, -W1_HI / ln2 - 2.0))
     lines.append("")
+    lines.append("// INV1S from L' = log2(256 r (1-r)), Horner in L' itself, valid for L' > kINV1SLmin")
+    lines.append("constexpr float kINV1SLmin = -6.0f;")
+    lines.append("")
     for p in pieces:
         lines.append("// %s: %s; fit max error %.2e, in float32 %.2e" % (p["name"], p["note"], p["fit_err"],
                                                                          p["f32_err"]))
@@ -147,6 +172,7 @@ def main():
     pieces = [
         fit_phi(9),
         fit_inv("INV1", 0.0, W1_HI, "w", 10),
+        fit_inv1_scaled(10),
         fit_inv("INV2", W1_HI, 36.0, "s", 9),
         fit_inv("INV3", 36.0, 130.0, "s", 8),
         fit_inv("INV4", 130.0, 700.0, "s", 8),

@@ -64,13 +64,14 @@ struct GenzSmem {
     // Recursion tables, step t (lattice coordinate t, variable t + 1 next):
     //   Lz[t]      = L_{t+1,t}          coefficient of y_t in variable t+1
     //   Lup[t][r]  = L_{t+2+r,t}        coefficients of y_t in the later variables
-    // MIXED divides each row v by L_vv (so the conditional mean is already
-    // standardised); FP64 keeps them unscaled and multiplies the conditional
-    // mean by 1/L_vv (diag), one rounding more than the definition's division.
+    // MIXED multiplies each row v by kZs/L_vv (so the conditional mean arrives
+    // standardised and times kZs = sqrt(log2(e)/2), the form its Phi takes);
+    // FP64 keeps them unscaled and multiplies the conditional mean by 1/L_vv
+    // (diag), one rounding more than the definition's division.
     static constexpr int LS = (DMAX + 3) & ~3;  // row stride: 16-byte aligned rows
     __align__(16) T Lup[DMAX][LS];
     __align__(16) T Lz[DMAX];
-    __align__(16) T up[DMAX];  // MIXED: u_v / L_vv;  FP64: u_v
+    __align__(16) T up[DMAX];  // MIXED: kZs u_v / L_vv;  FP64: u_v
     uint32_t gl[DMAX];         // FP64: g_t;  MIXED: round(g_t 2^32 / N)
     uint64_t g64[MIXED ? 1 : DMAX];  // FP64: round(g_t 2^64 / N)
     double part_num[kMaxUnits], part_den[kMaxUnits];
@@ -198,10 +199,10 @@ __device__ __forceinline__ void mixed_steps(const GenzSmem<DMAX, true>& sm, cons
             } else {  // w e_t below 2^-64: from log2(w e_t)
                 y = special::phiinv_log2(special::lg2(w) + L.le2[p]);
             }
-            const float z = fmaf(-lz, y, L.R[p][0]);
+            const float z = fmaf(-lz, y, L.R[p][0]);  // kZs z (the tables carry kZs)
 #pragma unroll
             for (int r = 0; r < W; ++r) L.R[p][r] = fmaf(-lup[r], y, L.R[p][r + 1]);
-            special::phi_pair(z, L.e[p], L.ec[p], L.tiny[p], L.le2[p]);
+            special::phi_pair_s(z, L.e[p], L.ec[p], L.tiny[p], L.le2[p]);
         }
     }
 }
@@ -296,12 +297,12 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
     if constexpr (P == 1) {  // one point per lane: the per-point form keeps fewer values live
         if (!FIRST) g[0] = __fmul_rn(g[0], e[0]);
         const uint32_t X = kk[0] * G + Dt;
-        const float w = __fmul_rn(fabsf(__int2float_rn((int32_t)X)), 0x1p-31f);  // |int32(X)| 2^-31
-        const float yv = special::phiinv_pq(__fmul_rn(w, e[0]), fmaf(w, ec[0], __fsub_rn(1.0f, w)));
+        const float wk = __fmul_rn(fabsf(__int2float_rn((int32_t)X)), 0x1p-27f);  // 16 w
+        const float yv = special::phiinv16_pq(__fmul_rn(wk, e[0]), fmaf(wk, ec[0], __fsub_rn(16.0f, wk)));
         const float z = fmaf(nlz, yv, R[0][0]);
 #pragma unroll
         for (int r = 0; r < W; ++r) R[0][r] = fmaf(-lup[r], yv, R[0][r + 1]);
-        special::phi_pair_fast(z, e[0], ec[0]);
+        special::phi_pair_fast_s(z, e[0], ec[0]);
         return;
     }
     // Phi^{-1} of every point's w_t e_t first, so one full-warp vote decides
@@ -313,25 +314,27 @@ __device__ __forceinline__ void fast_step(const GenzSmem<DMAX, true>& sm, const 
     for (int p = 0; p < P; ++p) {
         if (!FIRST) g[p] = __fmul_rn(g[p], e[p]);  // g = e_1 ... e_t
         // lattice coordinate in 32-bit fixed point, tent transform w = 1 - |2x - 1|
-        // of x = X 2^-32: exactly |int32(X)| 2^-31 (the sign folds into the product)
+        // of x = X 2^-32: exactly |int32(X)| 2^-31 (the sign folds into the
+        // product); carried as 16 w, 16 w e and 16 (1 - w e), exact scalings
+        // that give the quantile's polynomial its variable directly
         const uint32_t X = kk[p] * G + Dt;
-        const float w = __fmul_rn(fabsf(__int2float_rn((int32_t)X)), 0x1p-31f);
-        pp[p] = __fmul_rn(w, e[p]);
-        qq[p] = fmaf(w, ec[p], __fsub_rn(1.0f, w));
-        y[p] = special::phiinv_central(pp[p], qq[p], tail[p]);
+        const float wk = __fmul_rn(fabsf(__int2float_rn((int32_t)X)), 0x1p-27f);
+        pp[p] = __fmul_rn(wk, e[p]);
+        qq[p] = fmaf(wk, ec[p], __fsub_rn(16.0f, wk));
+        y[p] = special::phiinv16_central(pp[p], qq[p], tail[p]);
         any_tail = any_tail || tail[p];
     }
     if (__any_sync(0xffffffffu, any_tail)) {
 #pragma unroll
-        for (int p = 0; p < P; ++p) y[p] = special::phiinv_with_tail(pp[p], qq[p], tail[p], y[p]);
+        for (int p = 0; p < P; ++p) y[p] = special::phiinv16_with_tail(pp[p], qq[p], tail[p], y[p]);
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const float yv = special::phiinv_finish(pp[p], qq[p], y[p]);
-        const float z = fmaf(nlz, yv, R[p][0]);
+        const float z = fmaf(nlz, yv, R[p][0]);  // kZs z (the tables carry kZs)
 #pragma unroll
         for (int r = 0; r < W; ++r) R[p][r] = fmaf(-lup[r], yv, R[p][r + 1]);
-        special::phi_pair_fast(z, e[p], ec[p]);
+        special::phi_pair_fast_s(z, e[p], ec[p]);
     }
 }
 
@@ -379,16 +382,18 @@ __device__ __forceinline__ void genz_points_fast(const GenzSmem<DMAX, true>& sm,
         sc[t] = make_float4(-sm.Lz[t], __uint_as_float(sm.gl[t]), __uint_as_float(dfs[t]), 0.0f);
     __syncwarp();
     const float e0f = (float)sm.e0, ec0f = (float)sm.ec0;
+    // point indices in 32 bits: N <= 2^31 - 1, so kb + 32 P stays below 2^32
+    const uint32_t k_lo = (uint32_t)k_begin, k_hi = (uint32_t)k_end;
     Kahan32 kn, kd;
-    for (int64_t kb = k_begin; kb < k_end; kb += 32 * P) {
+    for (uint32_t kb = k_lo; kb < k_hi; kb += 32 * P) {
         float R[P][DMAX - 1], e[P], ec[P], g[P], gd[P];
         uint32_t kk[P];
         bool valid[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int64_t k = kb + p * 32 + lane;
-            valid[p] = k < k_end;
-            kk[p] = (uint32_t)(valid[p] ? k : k_begin);
+            const uint32_t k = kb + p * 32 + lane;
+            valid[p] = k < k_hi;
+            kk[p] = valid[p] ? k : k_lo;
 #pragma unroll
             for (int r = 0; r < DMAX - 1; ++r) R[p][r] = sm.up[1 + r];
             e[p] = e0f;
@@ -739,11 +744,13 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
 
         if (!sm.bad) {
             // ---- derived tables for the recursion ----
-            // (one FP64 reciprocal 1/L_vv per row; mixed: each row scaled by it)
+            // (one FP64 reciprocal 1/L_vv per row; mixed: each row scaled by
+            // kZs/L_vv, so the recursion's conditional means arrive as the
+            // kZs z that its Phi takes)
             constexpr int LS = GenzSmem<DMAX, MIXED>::LS;
             const int d = q + 1;
             for (int v = threadIdx.x; v < DMAX; v += blockDim.x)
-                sm.diag[v] = (v < d) ? 1.0 / sm.A[v][v] : 0.0;
+                sm.diag[v] = (v < d) ? (MIXED ? special::kZsD : 1.0) / sm.A[v][v] : 0.0;
             __syncthreads();
             for (int x = threadIdx.x; x < DMAX * LS; x += blockDim.x) {
                 const int t = x / LS, r = x % LS, v = t + 2 + r;
@@ -992,6 +999,9 @@ __global__ void eval_special_kernel(int which, const float* __restrict__ x, int6
         case 2: special::phi_pair(v, e, ec, tiny, le2); r = tiny ? le2 : NAN; break;
         case 3: r = special::phiinv_pq(v, 1.0f - v); break;
         case 4: r = special::phiinv_log2(v); break;
+        case 5: special::phi_pair_fast_s(v, e, ec); r = e; break;
+        case 6: special::phi_pair_fast_s(v, e, ec); r = ec; break;
+        case 7: r = special::phiinv16_pq(__fmul_rn(16.0f, v), __fmul_rn(16.0f, __fsub_rn(1.0f, v))); break;
         default: r = NAN;
     }
     out[i] = r;

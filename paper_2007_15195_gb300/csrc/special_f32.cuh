@@ -14,6 +14,9 @@ constexpr float kZmax = 38.0f;
 // INV1 from L = log2(r (1-r)): u = kINV1LA L + kINV1LB, valid for L > kINV1Lmin
 constexpr float kINV1LA = -1.732867951e-01f, kINV1LB = -1.346573590e+00f, kINV1Lmin = -1.354156033e+01f;
 
+// INV1S from L' = log2(256 r (1-r)), Horner in L' itself, valid for L' > kINV1SLmin
+constexpr float kINV1SLmin = -6.0f;
+
 // PHI: log2 exponent; relative error of Phi; fit max error 7.38e-08, in float32 2.09e-07
 constexpr float kPHIA = 2.148864586e+00f, kPHIB = -1.148864586e+00f;
 constexpr int kPHIN = 10;
@@ -23,6 +26,11 @@ __device__ constexpr float kPHIC[10] = {-1.901662401e+00f, 9.110765296e-01f, 4.6
 constexpr float kINV1A = 2.500000000e-01f, kINV1B = -1.000000000e+00f;
 constexpr int kINV1N = 11;
 __device__ constexpr float kINV1C[11] = {2.628710547e+00f, 1.291766786e+00f, -1.633898537e-01f, -1.841084796e-02f, 4.300585238e-02f, -2.277074509e-02f, 2.914623517e-03f, 4.860883741e-03f, -3.243484563e-03f, -1.816164950e-04f, 5.808041748e-04f};
+
+// INV1S: sqrt(2) erfinv(y)/y / 16 as a polynomial in L' = log2(256 r (1-r)), w in [0, 8.31777]; fit max error 1.30e-07, in float32 2.96e-07
+constexpr float kINV1SA = 1.000000000e+00f, kINV1SB = 0.000000000e+00f;
+constexpr int kINV1SN = 11;
+__device__ constexpr float kINV1SC[11] = {1.674851056e-01f, -1.384895821e-02f, -3.100284359e-04f, 3.872862671e-06f, 2.174756666e-06f, 2.151596011e-07f, 6.789406408e-09f, -1.169283648e-09f, -1.575603574e-10f, 2.953243844e-13f, 7.592575372e-13f};
 
 // INV2: sqrt(2) erfinv(y)/y on s in [2.82843, 6]; fit max error 4.91e-08, in float32 1.41e-07
 constexpr float kINV2A = 6.306019375e-01f, kINV2B = -2.783611625e+00f;

@@ -105,6 +105,39 @@ __device__ __forceinline__ void phi_pair_fast(float z, float& e, float& ec) {
     ec = neg ? __fsub_rn(1.0f, tail) : tail;
 }
 
+// The same Phi for the mixed Genz step, whose recursion tables carry the
+// factor kZs = sqrt(log2(e)/2) (folded into each row's FP64 scaling): from
+// zs = kZs z the exponent -z^2 log2(e)/2 is the single fma -zs zs + P(t), and
+// t = 1/(1 + z kKt) = 1/(1 + zs kKtS).  Same t and exponent as phi_pair and
+// phi_pair_fast up to the FP32 rounding of zs.
+constexpr double kZsD = 0.84932180028801904272;  // sqrt(log2(e) / 2)
+constexpr float kZs = (float)kZsD;
+constexpr float kKtS = (float)(0.35355339059327376220 / kZsD);   // 1 / (2 sqrt(2) kZs)
+constexpr float kZmaxS = (float)(38.0 * kZsD);
+constexpr float kTinyZS = (float)(-9.0 * kZsD);
+
+__device__ __forceinline__ void phi_pair_s(float zs, float& e, float& ec, bool& tiny, float& le2) {
+    const float az = fminf(fabsf(zs), kZmaxS);
+    const float t = rcp(fmaf(az, kKtS, 1.0f));
+    const float a = fmaf(-az, az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float tail = __fmul_rn(t, ex2(a));
+    const bool neg = zs < 0.0f;
+    e = neg ? tail : __fsub_rn(1.0f, tail);
+    ec = neg ? __fsub_rn(1.0f, tail) : tail;
+    tiny = zs < kTinyZS;
+    if (tiny) le2 = lg2(t) + a;
+}
+
+__device__ __forceinline__ void phi_pair_fast_s(float zs, float& e, float& ec) {
+    const float az = fabsf(zs);
+    const float t = rcp(fmaf(az, kKtS, 1.0f));
+    const float a = fmaf(-az, az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float tail = __fmul_rn(t, ex2(a));
+    const bool neg = zs < 0.0f;
+    e = neg ? tail : __fsub_rn(1.0f, tail);
+    ec = neg ? __fsub_rn(1.0f, tail) : tail;
+}
+
 // f_s(w) = sqrt(2) erfinv(y)/y for w >= 8 (sqrt(w) pieces).
 __device__ __forceinline__ float finv_tail(float w) {
     const float s = sqrt_approx(w);  // w = +inf gives s = +inf: the last piece at its end
@@ -144,6 +177,30 @@ __device__ __forceinline__ float phiinv_with_tail(float p, float q, bool tail, f
 }
 __device__ __forceinline__ float phiinv_finish(float p, float q, float f) {
     return __fmul_rn(__fsub_rn(p, q), f);
+}
+
+// Phi^{-1}(p) from pk = 16 p and qk = 16 q, as the mixed Genz step carries
+// them (16 w = |int32(X)| 2^-27 is as exact as w, and so are 16 w e and
+// 16 (1 - w e)): L' = log2(pk qk) = log2(p q) + 8 is the central polynomial's
+// variable as it stands (kINV1SC: fitted on w = -ln 2 (L' - 6) in
+// [0, 12 ln 2], where the map to [-1, 1] is -L'/6 with no offset, folded into
+// the coefficients with the factor 1/16), so that Phi^{-1}(p) = (pk - qk) f.
+// Split as phiinv_central / phiinv_with_tail for one vote over several values.
+__device__ __forceinline__ float phiinv16_central(float pk, float qk, bool& tail) {
+    const float L = lg2(__fmul_rn(pk, qk));
+    tail = !(L > kINV1SLmin);
+    return horner(kINV1SC, L);
+}
+__device__ __forceinline__ float phiinv16_with_tail(float pk, float qk, bool tail, float f) {
+    const float L = lg2(__fmul_rn(pk, qk));
+    const float ft = __fmul_rn(finv_tail(fmaf(-kLn2, L, 6.0f * kLn2)), 0.0625f);
+    return tail ? ft : f;
+}
+__device__ __forceinline__ float phiinv16_pq(float pk, float qk) {
+    bool tail;
+    float f = phiinv16_central(pk, qk, tail);
+    if (__any_sync(__activemask(), tail)) f = phiinv16_with_tail(pk, qk, tail, f);
+    return __fmul_rn(__fsub_rn(pk, qk), f);
 }
 
 // Phi^{-1}(r) for r = 2^lr2 < 2^-64 (log2 input).

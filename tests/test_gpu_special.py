@@ -43,6 +43,39 @@ def test_phi_relative_error_of_the_smaller_tail(ctx):
     assert np.max(np.abs(e - ref)) < 2e-7
 
 
+KZS = np.sqrt(np.log2(np.e) / 2.0)  # the fast mixed step carries kZs z
+
+
+def test_phi_scaled_form_of_the_fast_step(ctx):
+    """Phi from zs = kZs z (one fma for the exponent): the same accuracy as
+    the unscaled form, for z = zs / kZs."""
+    zs = np.linspace(-9.0, 9.0, 200001) * KZS
+    e, zf = _run(ctx, 5, zs)
+    ec, _ = _run(ctx, 6, zs)
+    x = zf / KZS
+    ref, refc = special.ndtr(x), special.ndtr(-x)
+    small = np.where(x < 0, e, ec)
+    small_ref = np.where(x < 0, ref, refc)
+    a = 0.5 * x * x * np.log2(np.e)
+    bound = 8e-7 + 1.2e-7 * np.maximum(a, 1.0)
+    assert np.all(np.abs(small - small_ref) / small_ref < bound)
+    assert np.max(np.abs(e - ref)) < 2e-7
+    assert np.all(e + ec == pytest.approx(1.0, abs=1.2e-7))
+
+
+def test_quantile_scaled_form_of_the_fast_step(ctx):
+    """Phi^{-1} from 16 p and 16 q, the central polynomial in log2(256 p q)."""
+    p = np.concatenate([10.0 ** -np.linspace(37.5, 0.31, 20001), np.linspace(0.49, 0.999999, 20001)])
+    y, pf = _run(ctx, 7, p)
+    qf = (1.0 - pf.astype(np.float32)).astype(np.float64)
+    ref = np.where(pf <= 0.5, special.ndtri(pf), -special.ndtri(qf))
+    err = np.abs(y - ref) / np.maximum(1.0, np.abs(ref))
+    assert np.max(err) < 2e-6
+    # the central piece (p q > 2^-14.3) on its own: fit and FP32 evaluation
+    central = pf * qf > 2.0 ** -14.3
+    assert np.max(err[central]) < 8e-7
+
+
 def test_log2_phi_far_tail(ctx):
     x = np.linspace(-37.5, -9.01, 50001)
     l2, xf = _run(ctx, 2, x)
