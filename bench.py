@@ -59,10 +59,10 @@ def workload_for(m):
 #          ALG_OPS_STEP FP32 operations of the formulation the kernel evaluates
 #          -- lattice coordinate and tent map 5 (scale, 16 - 16w, 16 w e,
 #          16 q, running product), Phi^{-1} 13 (p q, 10 fma of the polynomial
-#          in log2(256 p q) itself, p - q, scale), Phi 14 (1 + |zs| k, map of
-#          t, 9-term polynomial, exponent -zs^2 + P as one fma, t 2^a,
-#          1 - tail) -- plus (t + 1) FMAs for the conditional mean of row
-#          t + 1, i.e. q(q+1)/2 FMAs per point of a q-neighbour term.
+#          in log2(256 p q) itself, p - q, scale), Phi 13 (1 + |zs| k, 9 fma
+#          of the polynomial in t itself, exponent -zs^2 + P as one fma,
+#          t 2^a, 1 - tail) -- plus (t + 1) FMAs for the conditional mean of
+#          row t + 1, i.e. q(q+1)/2 FMAs per point of a q-neighbour term.
 #          Selects, min/max, integer and special-function-unit instructions
 #          are not counted.
 SM_COUNT = 152          # replaced by the device's SM count (init_peaks)
@@ -73,7 +73,7 @@ PEAK_SOURCE = "GB300 nominal: 152 SMs, 2070 MHz"
 # FP32 rate (1.25 TFLOP/s FP64 nominal = 152 SMs x 2 FMA lanes x 2 flops x
 # 2.07 GHz).
 FP64_LANES_PER_SM = 2
-ALG_OPS_STEP = 32
+ALG_OPS_STEP = 31
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the Genz kernel on the headline workload (m = 20, built-in tile:
 # genz_kernel<21, 2, fast>), from one ncu capture of that launch.

@@ -17,10 +17,10 @@ constexpr float kINV1LA = -1.732867951e-01f, kINV1LB = -1.346573590e+00f, kINV1L
 // INV1S from L' = log2(256 r (1-r)), Horner in L' itself, valid for L' > kINV1SLmin
 constexpr float kINV1SLmin = -6.0f;
 
-// PHI: log2 exponent; relative error of Phi; fit max error 7.38e-08, in float32 2.09e-07
-constexpr float kPHIA = 2.148864586e+00f, kPHIB = -1.148864586e+00f;
+// PHI: log2 exponent as a polynomial in t itself; relative error of Phi; fit max error 7.38e-08, in float32 2.16e-07
+constexpr float kPHIA = 1.000000000e+00f, kPHIB = 0.000000000e+00f;
 constexpr int kPHIN = 10;
-__device__ constexpr float kPHIC[10] = {-1.901662401e+00f, 9.110765296e-01f, 4.667263129e-02f, -5.721033787e-02f, -7.310898574e-03f, 9.311577214e-03f, 7.124167869e-04f, -1.848043810e-03f, 2.924683791e-06f, 2.557072991e-04f};
+__device__ constexpr float kPHIC[10] = {-2.825746561e+00f, 1.442697133e+00f, 5.398850582e-01f, 1.395404485e-01f, -2.716838926e-01f, 4.150338577e-01f, -1.662797825e+00f, 2.173985704e+00f, -1.200732298e+00f, 2.498184801e-01f};
 
 // INV1: sqrt(2) erfinv(y)/y on w in [0, 8]; fit max error 8.68e-08, in float32 1.93e-07
 constexpr float kINV1A = 2.500000000e-01f, kINV1B = -1.000000000e+00f;

@@ -84,7 +84,7 @@ __device__ __forceinline__ float horner(const float (&c)[N], float u) {
 __device__ __forceinline__ void phi_pair(float z, float& e, float& ec, bool& tiny, float& le2) {
     const float az = fminf(fabsf(z), kZmax);
     const float t = rcp(fmaf(az, kKt, 1.0f));
-    const float a = fmaf(__fmul_rn(az, -0.5f * kLog2e), az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float a = fmaf(__fmul_rn(az, -0.5f * kLog2e), az, horner(kPHIC, t));
     const float tail = __fmul_rn(t, ex2(a));  // Phi(-|z|)
     const bool neg = z < 0.0f;
     e = neg ? tail : __fsub_rn(1.0f, tail);
@@ -98,7 +98,7 @@ __device__ __forceinline__ void phi_pair(float z, float& e, float& ec, bool& tin
 __device__ __forceinline__ void phi_pair_fast(float z, float& e, float& ec) {
     const float az = fabsf(z);
     const float t = rcp(fmaf(az, kKt, 1.0f));
-    const float a = fmaf(__fmul_rn(az, -0.5f * kLog2e), az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float a = fmaf(__fmul_rn(az, -0.5f * kLog2e), az, horner(kPHIC, t));
     const float tail = __fmul_rn(t, ex2(a));
     const bool neg = z < 0.0f;
     e = neg ? tail : __fsub_rn(1.0f, tail);
@@ -119,7 +119,7 @@ constexpr float kTinyZS = (float)(-9.0 * kZsD);
 __device__ __forceinline__ void phi_pair_s(float zs, float& e, float& ec, bool& tiny, float& le2) {
     const float az = fminf(fabsf(zs), kZmaxS);
     const float t = rcp(fmaf(az, kKtS, 1.0f));
-    const float a = fmaf(-az, az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float a = fmaf(-az, az, horner(kPHIC, t));
     const float tail = __fmul_rn(t, ex2(a));
     const bool neg = zs < 0.0f;
     e = neg ? tail : __fsub_rn(1.0f, tail);
@@ -131,7 +131,7 @@ __device__ __forceinline__ void phi_pair_s(float zs, float& e, float& ec, bool& 
 __device__ __forceinline__ void phi_pair_fast_s(float zs, float& e, float& ec) {
     const float az = fabsf(zs);
     const float t = rcp(fmaf(az, kKtS, 1.0f));
-    const float a = fmaf(-az, az, horner(kPHIC, fmaf(t, kPHIA, kPHIB)));
+    const float a = fmaf(-az, az, horner(kPHIC, t));
     const float tail = __fmul_rn(t, ex2(a));
     const bool neg = zs < 0.0f;
     e = neg ? tail : __fsub_rn(1.0f, tail);

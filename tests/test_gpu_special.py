@@ -40,7 +40,10 @@ def test_phi_relative_error_of_the_smaller_tail(ctx):
     a = 0.5 * xf * xf * np.log2(np.e)
     bound = 8e-7 + 1.2e-7 * np.maximum(a, 1.0)
     assert np.all(np.abs(small - small_ref) / small_ref < bound)
-    assert np.max(np.abs(e - ref)) < 2e-7
+    # near Phi = 1/2 the exponent a ~ -2 carries a few FP32 roundings of its
+    # Horner sum (~2 ulp of 2, 1.6e-7 relative after ln 2) on top of the fit:
+    # about 4 ulp of 1/2 in absolute terms
+    assert np.max(np.abs(e - ref)) < 2.5e-7
 
 
 KZS = np.sqrt(np.log2(np.e) / 2.0)  # the fast mixed step carries kZs z
@@ -59,7 +62,7 @@ def test_phi_scaled_form_of_the_fast_step(ctx):
     a = 0.5 * x * x * np.log2(np.e)
     bound = 8e-7 + 1.2e-7 * np.maximum(a, 1.0)
     assert np.all(np.abs(small - small_ref) / small_ref < bound)
-    assert np.max(np.abs(e - ref)) < 2e-7
+    assert np.max(np.abs(e - ref)) < 2.5e-7
     assert np.all(e + ec == pytest.approx(1.0, abs=1.2e-7))
 
 
