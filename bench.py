@@ -77,7 +77,7 @@ ALG_OPS_STEP = 31
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the Genz kernel on the headline workload (m = 20, built-in tile:
 # genz_kernel<21, 2, fast>), from one ncu capture of that launch.
-GENZ_TRAFFIC_BYTES_M20 = None
+GENZ_TRAFFIC_BYTES_M20 = 365_312
 # DRAM bytes of one launch of the FP64 Genz kernel on the headline workload
 # (genz_kernel<21, 1, FP64>), from one ncu capture of that launch.
 GENZ64_TRAFFIC_BYTES_M20 = 497_408
