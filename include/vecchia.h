@@ -311,9 +311,12 @@ int vecchia_mixture_log_cdf(vecchia_ctx* ctx, const double* sites_ordered, int64
  * same rank-1 lattice (dimension D - 1) and shifts as the Vecchia terms: the
  * m = D - 1 limit of Eq. (vecchia-cdf), which telescopes (Eq.
  * cascading-conditional-cdf) -- the estimate the approximation is compared
- * with.  Covariance and Cholesky in FP64 (blocked; each entry of the factor
- * takes its terms in ascending order with fma, then the pivot division);
- * the recursion over all D variables in the precision requested (mixed: FP32
+ * with.  Covariance and Cholesky in FP64 (blocked, 32 columns a block; FP64
+ * path: each entry of the factor takes its terms in ascending order with fma,
+ * then the pivot division; mixed path: the same, except that the trailing
+ * update of each block column runs on the tensor cores from bf16 digit slices
+ * of the block column at FP64 accuracy, see vecchia_full_cholesky); the
+ * recursion over all D variables in the precision requested (mixed: FP32
  * integrand, conditional means on the tensor cores from TF32 hi/lo splits of
  * the FP32 operands -- FP32-level accuracy --, FP64 running product and
  * sums).  log_p = log of the mean over shifts of the lattice means; rel_se =
@@ -327,6 +330,21 @@ int vecchia_mixture_log_cdf(vecchia_ctx* ctx, const double* sites_ordered, int64
 int vecchia_full_genz(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, vecchia_cov cov,
                       const double* u, int64_t N, int S, uint64_t seed, int precision, double* log_p,
                       double* rel_se);
+
+/* Diagnostic: the covariance of D sites (D x 2, host or device) and its
+ * Cholesky factor as vecchia_full_genz computes them, into L (D x D row-major,
+ * host or device, caller-owned): the lower triangle gets the factor, the
+ * strict upper triangle zeros.  precision VECCHIA_FP64: the FP64 blocked
+ * factor; VECCHIA_MIXED: each block column's trailing update on the tensor
+ * cores -- its rows written as 2^e times seven balanced base-256 digits
+ * (bf16), the digit products of each significance summed exactly in FP32
+ * accumulators, recombined in 64-bit integers and subtracted with one FP64
+ * rounding (error below a few 2^-53 of sum_t |L_rt L_ct|).  D <=
+ * VECCHIA_FULL_MAX_D.  VECCHIA_ERR_NOT_PD with the failing row in
+ * vecchia_last_error_site(); VECCHIA_ERR_TIMEOUT if a bounded device wait of
+ * the tensor-core update ran out. */
+int vecchia_full_cholesky(vecchia_ctx* ctx, const double* sites_ordered, int64_t D, vecchia_cov cov,
+                          int precision, double* L);
 
 /* The censored likelihood G_I of Sec. 4 (Eq. model05) for one replicate:
  * the nc censored values (sites_c ordered, x_c, neighbour rows nbr nc x m

@@ -109,6 +109,7 @@ def lib():
                                               C.POINTER(C.c_double)]
         L.vecchia_full_genz.argtypes = [_vp, _vp, C.c_int64, vecchia_cov, _vp, C.c_int64, C.c_int, C.c_uint64,
                                         C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.vecchia_full_cholesky.argtypes = [_vp, _vp, C.c_int64, vecchia_cov, C.c_int, _vp]
         L.vecchia_censored_log_cdf.argtypes = [_vp, _vp, C.c_int64, _vp, C.c_int, _vp, C.c_int64, vecchia_cov, _vp,
                                                _vp, C.c_int64, C.c_int, C.c_uint64, C.c_double, C.c_double,
                                                C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -323,6 +324,18 @@ def vecchia_full_genz(ctx, sites_ordered, cov, u, N, S, seed=0, precision=MIXED)
                                    C.c_uint64(int(seed)), int(precision), C.byref(lp), C.byref(se)),
            "vecchia_full_genz", ctx)
     return lp.value, se.value
+
+
+def vecchia_full_cholesky(ctx, sites_ordered, cov, precision=MIXED, out=None):
+    """Covariance factor behind vecchia_full_genz (diagnostic): returns the D x D
+    array (lower triangle the factor, upper zeros), numpy unless `out` (a CUDA
+    float64 tensor of D x D) is given."""
+    s = _f64(sites_ordered)
+    D = int(s.shape[0])
+    L = out if out is not None else np.empty((D, D), dtype=np.float64)
+    _check(lib().vecchia_full_cholesky(ctx.handle, _ptr(s), D, make_cov(cov), int(precision), _ptr(L)),
+           "vecchia_full_cholesky", ctx)
+    return L
 
 
 def vecchia_censored_log_cdf(ctx, sites_c, nbr, m, sites_i, cov, x_c, x_i, N, S, seed=0, beta=0.5, gamma=1.0,

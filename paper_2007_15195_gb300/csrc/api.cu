@@ -1453,6 +1453,55 @@ int vecchia_full_genz(vecchia_ctx* c, const double* sites, int64_t D, vecchia_co
     return VECCHIA_OK;
 }
 
+int vecchia_full_cholesky(vecchia_ctx* c, const double* sites, int64_t D, vecchia_cov cov, int precision,
+                          double* L) {
+    if (!c || !sites || !L || D < 1 || !cov_ok(cov)) return VECCHIA_ERR_ARG;
+    if (precision != VECCHIA_FP64 && precision != VECCHIA_MIXED) return VECCHIA_ERR_ARG;
+    if (D > VECCHIA_FULL_MAX_D) return VECCHIA_ERR_UNSUPPORTED;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VECCHIA_ERR_CUDA;
+    c->last_error_site = -1;
+    const bool mixed = precision == VECCHIA_MIXED;
+    const bool dev_in = is_device_ptr(sites), dev_out = is_device_ptr(L);
+    Carve dv(nullptr);
+    const size_t o_s = dv.off;
+    if (!dev_in) dv.take<double>(2 * D);
+    const size_t o_a = dv.off;
+    dv.take<double>((size_t)D * D);
+    const size_t o_t = dv.off;
+    if (mixed) dv.take<char>(vk::chol_tc_scratch_bytes(D));
+    const size_t o_b = dv.off;
+    dv.take<int>(2);
+    int st = ensure_arena(c, dv.off);
+    if (st != VECCHIA_OK) return st;
+    char* X = (char*)c->arena;
+    const double* sd = dev_in ? sites : (const double*)(X + o_s);
+    double* Ad = (double*)(X + o_a);
+    int* bd = (int*)(X + o_b);
+    const int status_init[2] = {INT_MAX, 0};
+    int status[2] = {INT_MAX, 0};
+    cudaError_t e = cudaSuccess;
+    if (!dev_in) e = cudaMemcpyAsync(X + o_s, sites, sizeof(double) * 2 * D, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Ad, 0, sizeof(double) * (size_t)D * D, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bd, status_init, sizeof(status_init), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = mixed ? vk::launch_cov_chol(sd, D, cov, Ad, bd, c->stream, X + o_t, bd + 1, c->full_wait_ns)
+                  : vk::launch_cov_chol(sd, D, cov, Ad, bd, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(L, Ad, sizeof(double) * (size_t)D * D,
+                            dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status, bd, sizeof(status), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VECCHIA_ERR_CUDA;
+    }
+    if (status[0] != INT_MAX) {
+        c->last_error_site = status[0];
+        return VECCHIA_ERR_NOT_PD;
+    }
+    return status[1] ? VECCHIA_ERR_TIMEOUT : VECCHIA_OK;
+}
+
 int vecchia_mixture_log_cdf(vecchia_ctx* c, const double* sites, int64_t D, const int32_t* nbr, int m,
                             vecchia_cov cov, const double* x, int64_t N, int S, uint64_t seed,
                             double beta, double gamma, int n_nodes, int precision, double* log_g,

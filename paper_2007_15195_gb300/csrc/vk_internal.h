@@ -144,8 +144,24 @@ cudaError_t launch_group_random(int64_t D, int p, int kk, uint64_t seed, int cma
 
 // Covariance of D device sites (FP64, lower triangle of the D x D array A) and
 // its blocked Cholesky factor in place; *bad = min failing row (start INT_MAX).
+// With tc_scratch (chol_tc_scratch_bytes(D) bytes) the trailing updates run on
+// the tensor cores at FP64 accuracy (chol_tc.cu); a device wait of theirs that
+// runs out sets *timeout.
 cudaError_t launch_cov_chol(const double* sites, int64_t D, const vecchia_cov& cov, double* A, int* bad,
-                            cudaStream_t st);
+                            cudaStream_t st, void* tc_scratch = nullptr, int* timeout = nullptr,
+                            uint64_t wait_ns = 2000000000ull);
+// The tensor-core trailing update (chol_tc.cu): a panel's rows as 7 bf16
+// digit matrices per group of 8 rows (kCholSliceGroupBytes a group) and their
+// exponents, written by the row solve; part 0 updates the next block column,
+// part 1 the rest of the trailing matrix below base.
+constexpr int kCholSlices = 7;
+constexpr uint32_t kCholSliceGroupBytes = kCholSlices * 512;
+size_t chol_tc_slice_bytes(int64_t D);
+size_t chol_tc_scratch_bytes(int64_t D);
+// Once per device, outside any stream capture: the update kernel's attributes.
+cudaError_t chol_tc_prepare();
+cudaError_t launch_chol_update_tc(const unsigned char* sl, const int* ex, double* A, int64_t D, int64_t base,
+                                  int part, int* timeout, uint64_t wait_ns, cudaStream_t st);
 // Conditioning on observed sites (censor.cu): with L the Cholesky factor of
 // Sigma_II (k x k, from launch_cov_chol on sites_i), rows a < nc of V
 // ((nc + 1) x k) get L^-1 Sigma_{I a}, row nc gets w = L^-1 x_I, and
