@@ -123,7 +123,7 @@ __device__ __forceinline__ void tile_of(int part, int nCb, int& R, int& Cb) {
     }
 }
 
-__global__ void __launch_bounds__(128) chol_update_tc_kernel(const unsigned char* __restrict__ sl,
+__global__ void __launch_bounds__(128, 1) chol_update_tc_kernel(const unsigned char* __restrict__ sl,
                                                              const int* __restrict__ ex, double* __restrict__ A,
                                                              int D, int base, int part, int* timeout,
                                                              uint64_t wait_ns) {
@@ -198,6 +198,16 @@ __global__ void __launch_bounds__(128) chol_update_tc_kernel(const unsigned char
                      : "memory");
     }
     __syncwarp();
+    // this thread's row of the output tile, loaded while the copies and MMAs
+    // run (the epilogue would otherwise wait on L2 or HBM for each chunk)
+    const int r = base + R * kTM + warp * 32 + lane;
+    const int c0 = base + Cb * kTN;
+    double Cv[kTN];
+    if (r < D) {
+        const double* row = A + (int64_t)r * D + c0;
+#pragma unroll
+        for (int j = 0; j < kTN; ++j) Cv[j] = (c0 + j <= r) ? row[j] : 0.0;
+    }
     if (!mbar_wait(&bar_mma, 0, wait_ns)) {
         atomicExch(timeout, 1);
         abort_flag = 1;
@@ -206,11 +216,9 @@ __global__ void __launch_bounds__(128) chol_update_tc_kernel(const unsigned char
     tc_fence_after();
     __syncthreads();
     if (!abort_flag) {  // CTA-uniform: the tensor-memory loads below are warp-collective
-        const int rr = warp * 32 + lane;
-        const int r = base + R * kTM + rr;
         const int er = (r < D) ? ex[r - base] : 0;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
+#pragma unroll
         for (int ch = 0; ch < kTN / 8; ++ch) {
             uint32_t G[kCholSlices][8];
 #pragma unroll
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(128) chol_update_tc_kernel(const unsigned char
                 double* row = A + (int64_t)r * D;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int c = base + Cb * kTN + ch * 8 + j;
+                    const int c = c0 + ch * 8 + j;
                     if (c > r || (part == 0 && r < base + kTN)) continue;  // part 0: not the diagonal block
                     // exact integers below 2^24 held as FP32
                     long long V = (long long)__float2int_rz(__uint_as_float(G[0][j]));
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(128) chol_update_tc_kernel(const unsigned char
                     const int e2 = er + ex[c - base] - 56;
                     if (e2 < -1020) continue;  // below 2^-1000 of the entries: nothing to subtract
                     const double scale = __hiloint2double((e2 + 1023) << 20, 0);
-                    row[c] = fma(-(double)V, scale, row[c]);
+                    row[c] = fma(-(double)V, scale, Cv[ch * 8 + j]);
                 }
             }
         }
