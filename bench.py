@@ -78,6 +78,11 @@ ALG_OPS_STEP = 31
 # the Genz kernel on the headline workload (m = 20, built-in tile:
 # genz_kernel<21, 2, fast>), from one ncu capture of that launch.
 GENZ_TRAFFIC_BYTES_M20 = 365_312
+# The same capture's pipe counters for the headline kernel (m = 20, built-in
+# tile): sm__pipe_fma_cycles_active and smsp__issue_active, and its issued
+# instructions per lattice step (smsp__inst_executed.sum x 32 / steps).
+GENZ_NCU_M20 = {"fma_pipe_active": 0.566, "issue_active": 0.773, "inst_per_step": 64.9,
+                "source": "ncu --set full of one genz_kernel<21, 2, 1> launch of this workload"}
 # DRAM bytes of one launch of the FP64 Genz kernel on the headline workload
 # (genz_kernel<21, 1, FP64>), from one ncu capture of that launch.
 GENZ64_TRAFFIC_BYTES_M20 = 497_408
@@ -490,7 +495,8 @@ def run_ours(args):
                          "ops": "FP32-pipe lane operations, an FMA counting once; %d per Genz step "
                                 "+ q(q+1)/2 FMAs per point; peak = %d SMs x %d lanes x %.0f MHz"
                                 % (ALG_OPS_STEP, SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ),
-                         "peak_source": PEAK_SOURCE},
+                         "peak_source": PEAK_SOURCE,
+                         "ncu": GENZ_NCU_M20 if m == 20 else None},
             "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step[V.MIXED] * args.steps,
