@@ -868,14 +868,17 @@ __global__ void __launch_bounds__(max_threads(DMAX, P, MODE)) __maxnreg__(reg_ca
 // ------------------------------- log-sum ------------------------------------
 // Two passes with a fixed reduction order, so results are bit-identical run to
 // run and alone vs in a batch:
-//   partial: CTA (slice, problem) takes sites slice*256 .. +255, forms each
+//   partial: CTA (slice, problem) takes sites slice*32 .. +31, forms each
 //     term T_i = log mean_s num - log mean_s den (Sec. 3.1: every term on the
 //     log scale) and the delta-method pieces num_is/numbar_i - den_is/denbar_i,
 //     and writes their slice sums;
 //   final: one warp per problem adds the slices in order and forms
 //     log P = sum_i T_i and SE = sqrt(sum_s l_s^2 / (S (S-1))).
 
-constexpr int kSliceSites = 256;
+// One warp a slice: the per-site work (two FP64 logarithms and the S
+// delta-method quotients) is FP64-bound on GB300, so a 2,500-site problem is
+// spread over 79 SMs rather than 10.
+constexpr int kSliceSites = kLogsumSlice;
 
 __device__ __forceinline__ double warp_sum_xor(double v) {
 #pragma unroll
@@ -909,7 +912,7 @@ __global__ void __launch_bounds__(kSliceSites) logsum_partial_kernel(
     }
     double v = warp_sum_xor(T);
     if (lane == 0) red[0][warp] = v;
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < S; ++s) {  // quotients, not products by reciprocals: equal shifts give exactly 0
         const double c = valid ? Pd.num[i * S + s] / a - Pd.den[i * S + s] / b : 0.0;
         v = warp_sum_xor(c);
         if (lane == 0) red[1 + s][warp] = v;

@@ -39,42 +39,61 @@ int grid_bits(int64_t D) {
     return k;
 }
 
+// Order-preserving integer image of a double (-0 taken as +0, as the
+// comparison x < y treats them): integer compares instead of FP64 ones, which
+// GB300 runs at 1/64 of its FP32 rate.
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x == 0.0 ? 0.0 : x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double ord_value(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k));
+}
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// Bounding box of the sites (one CTA): minima of the keys of x, y and of
+// their complements (the maxima), warp shuffles then one pass over the warps.
 __global__ void bbox_kernel(const double* __restrict__ sites, int64_t D, int gbits, Grid* out) {
-    __shared__ double sx0[1024], sx1[1024], sy0[1024], sy1[1024];
-    double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    __shared__ unsigned long long part[4][32];
+    unsigned long long k[4] = {~0ULL, ~0ULL, ~0ULL, ~0ULL};  // min x, min y, min ~x, min ~y
     for (int64_t i = threadIdx.x; i < D; i += blockDim.x) {
-        const double x = sites[2 * i], y = sites[2 * i + 1];
-        x0 = fmin(x0, x);
-        x1 = fmax(x1, x);
-        y0 = fmin(y0, y);
-        y1 = fmax(y1, y);
+        const unsigned long long kx = ord_key(sites[2 * i]), ky = ord_key(sites[2 * i + 1]);
+        k[0] = kx < k[0] ? kx : k[0];
+        k[1] = ky < k[1] ? ky : k[1];
+        k[2] = ~kx < k[2] ? ~kx : k[2];
+        k[3] = ~ky < k[3] ? ~ky : k[3];
     }
-    const int t = threadIdx.x;
-    sx0[t] = x0;
-    sx1[t] = x1;
-    sy0[t] = y0;
-    sy1[t] = y1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) k[q] = warp_min_u64(k[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) part[q][warp] = k[q];
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (t < o) {
-            sx0[t] = fmin(sx0[t], sx0[t + o]);
-            sx1[t] = fmax(sx1[t], sx1[t + o]);
-            sy0[t] = fmin(sy0[t], sy0[t + o]);
-            sy1[t] = fmax(sy1[t], sy1[t + o]);
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) k[q] = warp_min_u64(lane < nw ? part[q][lane] : ~0ULL);
+        if (lane == 0) {
+            const double xmin = ord_value(k[0]), ymin = ord_value(k[1]);
+            const double xmax = ord_value(~k[2]), ymax = ord_value(~k[3]);
+            const double ex = xmax - xmin, ey = ymax - ymin;
+            const double s = (ex > ey) ? ex : ey;
+            Grid g;
+            g.xmin = xmin;
+            g.ymin = ymin;
+            g.zero = !(s > 0.0);
+            g.c = g.zero ? 0.0 : 1073741824.0 / s;
+            g.shift = 30 - gbits;
+            g.G = 1 << gbits;
+            *out = g;
         }
-        __syncthreads();
-    }
-    if (t == 0) {
-        const double ex = sx1[0] - sx0[0], ey = sy1[0] - sy0[0];
-        const double s = (ex > ey) ? ex : ey;
-        Grid g;
-        g.xmin = sx0[0];
-        g.ymin = sy0[0];
-        g.zero = !(s > 0.0);
-        g.c = g.zero ? 0.0 : 1073741824.0 / s;
-        g.shift = 30 - gbits;
-        g.G = 1 << gbits;
-        *out = g;
     }
 }
 
@@ -820,17 +839,10 @@ cudaError_t launch_maxmin(const double* sites, int64_t D, int32_t* perm, void* s
 constexpr int kXyMax = 8192;
 constexpr int kXyThreads = 256;
 
-// Order-preserving integer image of a double (-0 taken as +0, as the
-// comparison x < y treats them): integer compares instead of FP64 ones.
-__device__ __forceinline__ unsigned long long ord_key(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x == 0.0 ? 0.0 : x);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
-}
-
 // Grid (site blocks x chunks of the other sites): each thread counts, for its
 // site, the smaller keys of one chunk and adds the count to rank[i] (integer
 // adds: the total does not depend on their order).
-constexpr int kXyChunk = 512;
+constexpr int kXyChunk = 128;  // 20 chunks at D = 2,500: a CTA for every SM
 
 __global__ void __launch_bounds__(kXyThreads) order_xy_rank_kernel(const double* __restrict__ sites, int D,
                                                                    int* __restrict__ rank) {

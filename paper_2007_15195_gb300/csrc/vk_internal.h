@@ -105,7 +105,8 @@ cudaError_t launch_genz_fallback(int max_bucket, const ProbDev* probs, const int
                                  int max_S, cudaStream_t st);
 // Per-problem deterministic log-sum and standard error over its n_terms terms;
 // writes results and terms.  scratch_off[p] points at logsum_scratch(n_terms_p, S_p) doubles.
-inline int64_t logsum_slices(int64_t D) { return (D + 255) / 256; }
+constexpr int kLogsumSlice = 32;  // sites per CTA of the log-sum's first pass
+inline int64_t logsum_slices(int64_t D) { return (D + kLogsumSlice - 1) / kLogsumSlice; }
 inline int64_t logsum_scratch(int64_t D, int S) { return logsum_slices(D) * (S + 1); }
 cudaError_t launch_logsum(const ProbDev* probs, int n_probs, int max_slices, ProbResult* results,
                           double* const* terms, double* scratch, const int64_t* scratch_off,
