@@ -892,6 +892,7 @@ def run_mixture(args):
     beta = 0.5, gamma = 1 (the paper fixes gamma = 1), 16 quadrature nodes:
     one step is one vecchia_mixture_log_cdf call from host arrays (a batch of
     16 Vecchia log-CDFs)."""
+    init_peaks(0)
     import torch
     import paper_2007_15195_gb300 as V
 
@@ -943,6 +944,7 @@ def run_grouped(args):
     on resident device arrays, its conditioning rows built once per config
     (their time is reported beside it).  The line's value is the p = 5,
     nearest configuration; every configuration is listed."""
+    init_peaks(0)
     import torch
     import paper_2007_15195_gb300 as V
     from paper_2007_15195_gb300 import inputs
@@ -1019,6 +1021,7 @@ def run_censored(args):
     mixing law beta = 0.5, gamma = 1 on 16 nodes.  One step = the censored
     log-likelihood: one vecchia_censored_log_cdf per replicate (resident
     device arrays), summed."""
+    init_peaks(0)
     import torch
     import paper_2007_15195_gb300 as V
     from paper_2007_15195_gb300 import inputs
